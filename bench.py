@@ -1,0 +1,329 @@
+"""Benchmark of the RMS random-walker step on GB300.
+
+One benchmark step = one whole simulation of the workload (walker
+initialisation, every time step with face walk / membrane crossing / phase /
+relaxation, the moment reductions and the signal read-out), with the label
+volume and sequence tables already resident in HBM.  The default workload is
+the 200 x 200 x 400 synthetic beaded-axon volume (0.1 um voxels, 200 axons,
+kappa = 0.01 um/ms), 1e6 walkers x 1e5 steps of dt = 2e-4 ms, 30 directions
+x 11 b-values.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own 1e6
+walkers (distinct global walker ids): weak scaling, no collective on the data
+path; the per-rank sums are combined after the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "walker-steps/s (FP64 plain vs FP32 form, |ΔS|≤1e-3); p50/p99 request latency"
+UNIT = "walker-steps/s"
+DEFAULT_WORKLOAD = "axons-200x200x400"
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 6:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx = float(p[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def flush_l2(torch, buf):
+    buf.add_(1.0)  # 256 MiB written: larger than the 129 MB L2
+
+
+def workload_of(name):
+    import rms_inputs as ri
+    return ri.workload(name)
+
+
+def events_per_step(wl):
+    """Expected face events per walker-step, 1.5 ds / l_p (walker-averaged
+    over labels by volume fraction; exact for any lattice)."""
+    lab = wl.labels
+    frac = np.bincount(lab.ravel(), minlength=wl.n_labels) / lab.size
+    ds = np.sqrt(6.0 * wl.D * wl.dt)
+    return float((frac * 1.5 * ds / wl.voxel_um).sum())
+
+
+def cpu_baseline(wl, seconds=12.0):
+    """The oracle as it stands on this host's cores, on a walker sample of the
+    same workload (walkers are independent: the sample's rate is the run's)."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    probe = max(cores, 16)
+    t0 = time.perf_counter()
+    oracle.run(wl, 0, probe, n_threads=cores, hash_=False)
+    dt = time.perf_counter() - t0
+    rate = probe * wl.n_steps / dt
+    W = max(cores, int(rate * seconds / wl.n_steps) // cores * cores)
+    t0 = time.perf_counter()
+    r = oracle.run(wl, 0, W, n_threads=cores, hash_=False)
+    oracle.readout(r, wl)
+    el = time.perf_counter() - t0
+    return {"value": W * wl.n_steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"walkers 0..{W - 1} x all {wl.n_steps} steps of {wl.name} (+ read-out), {el:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle timed as the reference arm (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload_of(args.workload)
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    probe = max(cores, 16)
+    t0 = time.perf_counter()
+    oracle.run(wl, 0, probe, n_threads=cores, hash_=False)
+    rate = probe * wl.n_steps / (time.perf_counter() - t0)
+    W = max(cores, int(rate * 8.0 / wl.n_steps) // cores * cores)  # ~8 s per step
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle.run(wl, it * W, (it + 1) * W, n_threads=cores, hash_=False)
+        oracle.readout(r, wl)
+        if it >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    el = sum(times)
+    value = args.steps * W * wl.n_steps / el
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "walkers_per_step": W, "steps_per_walker": wl.n_steps},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{W} walkers x {wl.n_steps} steps of {wl.name} per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64 plain-form steps")
+    ap.add_argument("--fp64-warmup", type=int, default=1, help="untimed FP64 plain-form steps")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2012_06478_gb300 as rms
+    from paper_2012_06478_gb300 import shard
+    wl = workload_of(args.workload)
+    W = wl.n_walkers
+    w_begin, _ = shard.shard_range(rank, world, W, weak=True)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    sub = rms.rms_create_substrate(wl.labels, wl.voxel_um, wl.D, T2=wl.T2, T1=wl.T1, kappa=wl.kappa,
+                                   dead=wl.dead, periodic=wl.periodic, stream=sp)
+    seq = rms.rms_set_sequence(sub, wl.dt, wl.G, wl.dirs, wl.b, wl.rec_steps, mode=wl.mode)
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    def timed(precision, n_warm, n_timed):
+        ev = []
+        res = None
+        walk_ms = []
+        for it in range(n_warm + n_timed):
+            flush_l2(torch, flush)
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run = rms.rms_run(seq, W, wl.seed, precision, 0, w_begin, 0, sp)
+            e1.record(stream)
+            res = rms.rms_read_signal(run)
+            if it >= n_warm:
+                ev.append(e0.elapsed_time(e1))
+                walk_ms.append(rms.rms_run_step_time_ms(run))
+            run.close()
+        barrier()
+        return ev, walk_ms, res
+
+    # FP32 form: the headline
+    with Clocks(local) as clk:
+        ms32, walk32, res32 = timed(rms.RMS_FP32, args.warmup, args.steps)
+    # FP64 plain form, same workload
+    ms64, walk64, res64 = timed(rms.RMS_FP64, args.fp64_warmup, args.fp64_steps)
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    t32 = max_over_ranks(sum(ms32))
+    t64 = max_over_ranks(sum(ms64))
+    ws = W * wl.n_steps
+    value = world * ws * args.steps / (t32 * 1e-3)
+    value64 = world * ws * args.fp64_steps / (t64 * 1e-3)
+    dS = float(np.abs(res32[0] - res64[0]).max())
+
+    # the one exchange step: combine the per-rank sums (not timed)
+    if world > 1:
+        v = shard.allreduce_partials(shard.pack_partials(res32[0], res32[2], res32[1]))
+        shard.unpack_partials(v, res32[0].shape, res32[1].shape)
+
+    spl = max(64, min(2_000_000_000 // W, wl.n_steps))
+    n_walk = math.ceil(wl.n_steps / spl)
+    launches_per_step = 1 + n_walk + (1 if wl.rec_steps.size else 0) + 3
+    walk_launch_ms = (sum(walk32) / len(walk32)) / n_walk
+    eps = events_per_step(wl)
+    alg_bytes = 2.0 * eps * W * spl  # label bytes per walk launch
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    achieved = alg_bytes / (walk_launch_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t32 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "walkers_per_gpu": W, "steps_per_walker": wl.n_steps, "dt_ms": wl.dt,
+                   "grid_xyz": list(wl.shape_xyz), "voxel_um": wl.voxel_um, "labels": wl.n_labels,
+                   "n_dirs": int(wl.dirs.shape[0]), "n_b": int(wl.b.size), "n_rec": int(wl.rec_steps.size),
+                   "precision": "fp32 form (headline); fp64 plain form in fp64_plain",
+                   "l2": "flushed between timed iterations (256 MiB write)", "parallelism": f"walker shards x{world}"},
+        "fp64_plain": {"value": value64, "unit": UNIT, "dtype": "f64", "steps": args.fp64_steps, "warmup": args.fp64_warmup,
+                       "ms_per_step": t64 / args.fp64_steps},
+        "max_abs_dS_fp32_vs_fp64": dS,
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if hbm else None, "traffic": None,
+                     "kernel": "walk_kernel<float,1,false>", "alg_bytes_per_walker_step": 2.0 * eps,
+                     "walker_steps_per_launch": W * spl, "launch_ms": walk_launch_ms,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+        "clocks": clk.summary(),
+    }
+    if not args.no_e2e:
+        line["e2e"] = e2e(rms, torch, wl, W, w_begin, sp, args, world, max_over_ranks)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    seq.close()
+    sub.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def e2e(rms, torch, wl, W, w_begin, sp, args, world, max_over_ranks):
+    """The same metric through the C ABI from host buffers: upload of the
+    label volume and tables, the run, the read-back of the signal and moments."""
+    lab = np.ascontiguousarray(wl.labels, np.uint16)
+    h2d = (lab.nbytes + wl.D.nbytes + wl.T2.nbytes + wl.T1.nbytes + wl.kappa.nbytes + wl.dead.nbytes +
+           np.asarray(wl.G).nbytes + wl.dirs.nbytes + wl.b.nbytes + wl.rec_steps.nbytes)
+    n_combo = np.asarray(wl.G).reshape(-1, wl.n_steps).shape[0] * wl.dirs.shape[0] * wl.b.size
+    d2h = 16 * n_combo + 8 * 22 * wl.rec_steps.size + 8
+    times = []
+    for it in range(1 + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sub = rms.rms_create_substrate(lab, wl.voxel_um, wl.D, T2=wl.T2, T1=wl.T1, kappa=wl.kappa, dead=wl.dead,
+                                       periodic=wl.periodic, stream=sp)
+        seq = rms.rms_set_sequence(sub, wl.dt, wl.G, wl.dirs, wl.b, wl.rec_steps, mode=wl.mode)
+        run = rms.rms_run(seq, W, wl.seed, rms.RMS_FP32, 0, w_begin, 0, sp)
+        rms.rms_read_signal(run)
+        el = time.perf_counter() - t0
+        run.close()
+        seq.close()
+        sub.close()
+        if it >= 1:
+            times.append(el)
+    t = max_over_ranks(sum(times))
+    return {"value": world * W * wl.n_steps * args.steps / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h)}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * rms.h -- C ABI of the GB300 random-walker engine for diffusion MRI Monte
+ * Carlo in voxelised cell segmentations, after Lee, Fieremans & Novikov,
+ * "Realistic Microstructure Simulator (RMS)", arXiv 2012.06478.
+ *
+ * The engine runs the method's data-parallel hot path on one GPU: walkers
+ * start uniformly over non-dead voxels (Sec. 2.2 item 1), take steps of
+ * length ds = sqrt(6 D dt) (Eq. 1) in Philox4x32-10 random directions, walk
+ * through voxel faces with at most three face events per step (Sec. 2.1.1,
+ * Fig. 2), cross a face between two labels with the finite-step corrected
+ * probability of Eq. 3 or are reflected specularly (Sec. 2.1.3), accumulate
+ * the phase of Eq. 7 and the relaxation weight of Eq. 5, and are reduced to
+ * the signal S(b, g) (Eq. 7) and the displacement moments behind the
+ * narrow-pulse D(t) and K(t) (Sec. 2.3).
+ *
+ * Conventions for every call:
+ *   - Plain C types and pointers only.  "host pointer" = ordinary process
+ *     memory; "device pointer" = memory on the current CUDA device.
+ *   - The library copies every input array; the caller keeps ownership and
+ *     may free its buffers as soon as the call returns.
+ *   - Handles own their device memory and free it on destroy.
+ *   - A `void *stream` is a cudaStream_t (NULL = the legacy default stream).
+ *     Work is enqueued on it asynchronously; calls that return results to
+ *     host memory synchronise with it.
+ *   - Every call returns an rms_status; on an error rms_last_error() gives a
+ *     message (per calling thread).  No C++ exception crosses this boundary.
+ *   - All handles belong to the device that was current when they were made;
+ *     use them with that device current.
+ */
+#ifndef RMS_H
+#define RMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int rms_status;
+
+#define RMS_OK 0
+#define RMS_W_PROB_RANGE 1        /* warning: some P_{1->2} of Eq. 3 exceeded 1 and was clamped */
+#define RMS_E_INVALID_ARG (-1)    /* a null pointer, a size out of range, an inconsistent array */
+#define RMS_E_OOM (-2)            /* a device or host allocation failed */
+#define RMS_E_CUDA (-3)           /* a CUDA runtime call failed (message has the CUDA error) */
+#define RMS_E_STEP_TOO_LARGE (-4) /* ds_c >= l_p for some label: a step could meet more than three faces */
+#define RMS_E_TIMEOUT (-6)        /* a bounded wait gave up */
+#define RMS_E_CANCELLED (-7)      /* the run was cancelled before it finished */
+#define RMS_E_BUSY (-8)           /* the handle is still referenced by a live sequence or run */
+#define RMS_E_DEVICE (-9)         /* a kernel reported a broken invariant (see message) */
+#define RMS_E_NOT_READY (-10)     /* the run is still in flight */
+
+/* precision forms of rms_run */
+#define RMS_FP64 0 /* plain form: FP64 positions and phases, no FMA; bit-exact trajectories */
+#define RMS_FP32 1 /* precision form: voxel index + FP32 offset, FP32 Kahan phase, FP64 reductions */
+
+/* rms_run flags */
+#define RMS_TRAJ_HASH 1u /* keep a per-walker 64-bit checksum of the (step, voxel, label) sequence */
+
+typedef struct rms_substrate rms_substrate;
+typedef struct rms_sequence rms_sequence;
+typedef struct rms_run_handle rms_run_handle;
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int rms_version(void);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *rms_last_error(void);
+
+/* ------------------------------------------------------------------ */
+/* Substrate: the voxelised label volume and per-label tissue tables.  */
+/* Sec. 2.1.1 (the label volume is its own lookup table), Sec. 2.1.3   */
+/* (D, kappa), Sec. 2.1.4 (T1, T2), Table 1.                           */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const uint16_t *labels;   /* nx*ny*nz labels, x fastest (index x + nx*(y + ny*z)) */
+    int32_t labels_on_device; /* 1: `labels` is a device pointer, 0: host pointer */
+    int32_t nx, ny, nz;       /* grid size, each >= 1, nx*ny*nz < 2^31 */
+    double voxel_um;          /* isotropic voxel edge l_p (um), > 0 */
+    int32_t periodic[3];      /* per axis: 1 periodic (lookups i mod N), 0 impermeable outer wall */
+    int32_t n_labels;         /* L: every label value is < L; 1 <= L <= 65536 */
+    const double *D;          /* host, L: intrinsic diffusivity (um^2/ms), > 0 */
+    const double *T2;         /* host, L or NULL: T2 (ms), INFINITY = none */
+    const double *T1;         /* host, L or NULL: T1 (ms), INFINITY = none */
+    const double *kappa;      /* host, L*L or NULL: permeability (um/ms) of the membrane from
+                                 label r (row) into label c (column); diagonal ignored */
+    double kappa_scalar;      /* used for every pair when kappa == NULL */
+    const uint8_t *dead;      /* host, L or NULL: 1 = no walker starts in or enters the label */
+    void *stream;             /* cudaStream_t for the upload */
+} rms_substrate_desc;
+
+/* Upload the volume and build the per-label tables.  Errors:
+ * RMS_E_INVALID_ARG, RMS_E_OOM, RMS_E_CUDA.  The permeation thresholds are
+ * built when a sequence fixes dt (rms_set_sequence). */
+rms_status rms_create_substrate(const rms_substrate_desc *desc, rms_substrate **out);
+
+/* Free the substrate.  RMS_E_BUSY (and nothing freed) while a sequence made
+ * from it is alive. */
+rms_status rms_destroy_substrate(rms_substrate *sub);
+
+/* ------------------------------------------------------------------ */
+/* Sequence: time step, gradient waveforms, read-out directions and    */
+/* b-values, recording steps.  Table 1 (dt, N_step), Eq. 7 (g(t)),     */
+/* Sec. 2.3 (b, directions).                                           */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double dt_ms;             /* time step (ms), > 0 */
+    int64_t n_steps;          /* N_step >= 0 */
+    int32_t n_shapes;         /* number of waveform shapes, 1..8 */
+    const double *G;          /* host, n_shapes*n_steps: effective gradient of unit amplitude,
+                                 the average of g(t)/|g| over step k (row = shape) */
+    const uint8_t *mode;      /* host, n_steps or NULL: relaxation during step k: 0 = T2, 1 = T1
+                                 (stimulated-echo mixing time), 2 = none */
+    int32_t n_dirs;           /* >= 1 */
+    const double *dirs;       /* host, n_dirs*3 unit gradient directions */
+    int32_t n_b;              /* >= 1 */
+    const double *b;          /* host, n_b b-values (ms/um^2), >= 0 */
+    int32_t n_rec;            /* >= 0 */
+    const int64_t *rec_steps; /* host, n_rec strictly increasing steps in [1, n_steps] at which
+                                 the displacement moments are recorded */
+} rms_sequence_desc;
+
+/* Validate and upload.  Builds ds_c = sqrt(6 D_c dt) (Eq. 1), the relaxation
+ * rates, the per-pair Bernoulli thresholds floor(P 2^32) from Eq. 3, and
+ * b_s = dt sum_j F_{j-1}^2 per shape.  Errors: RMS_E_INVALID_ARG,
+ * RMS_E_STEP_TOO_LARGE (ds_c >= l_p for a non-dead label, Sec. 2.1.1 and
+ * Table 1), RMS_E_OOM, RMS_E_CUDA.  Returns RMS_W_PROB_RANGE (with *out set)
+ * when some P_{1->2} > 1 had to be clamped (Eq. 3 assumes P << 1). */
+rms_status rms_set_sequence(rms_substrate *sub, const rms_sequence_desc *desc, rms_sequence **out);
+
+/* b_s of each shape (host pointer, n_shapes doubles); synchronises. */
+rms_status rms_sequence_bvalues(const rms_sequence *seq, double *b_s);
+
+/* RMS_E_BUSY while a run made from it is alive. */
+rms_status rms_destroy_sequence(rms_sequence *seq);
+
+/* ------------------------------------------------------------------ */
+/* Run                                                                  */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int64_t n_walkers;        /* W >= 1 */
+    int64_t walker_begin;     /* global id of the first walker (walkers are w_begin .. w_begin+W-1);
+                                 the random streams depend only on (seed, global id, step) */
+    uint64_t seed;            /* Philox key */
+    int32_t precision;        /* RMS_FP64 or RMS_FP32 */
+    uint32_t flags;           /* RMS_TRAJ_HASH or 0 */
+    int32_t steps_per_launch; /* steps per kernel launch (0 = default) */
+    void *stream;             /* cudaStream_t the whole run is enqueued on */
+} rms_run_desc;
+
+/* Allocate walker state and enqueue the whole simulation: initialisation
+ * (Sec. 2.2 item 1), every step (Sec. 2.2 items 2-5), the moment reductions
+ * and the signal read-out (Eq. 7).  Returns without waiting.  Errors:
+ * RMS_E_INVALID_ARG, RMS_E_OOM, RMS_E_CUDA. */
+rms_status rms_run(rms_sequence *seq, const rms_run_desc *desc, rms_run_handle **out);
+
+/* RMS_OK when the run has finished, RMS_E_NOT_READY while in flight. */
+rms_status rms_run_query(rms_run_handle *run);
+
+/* Ask a run to stop: launches not yet started do no work.  Reading it then
+ * returns RMS_E_CANCELLED. */
+rms_status rms_cancel(rms_run_handle *run);
+
+/* Wait for the run and copy results to host memory (any pointer may be NULL):
+ *   S_re, S_im : n_shapes*n_dirs*n_b, S = sum alpha e^{-i phi} / sum alpha
+ *                (index (shape*n_dirs + dir)*n_b + b)
+ *   moments    : n_rec*22 unnormalised sums over walkers at each recording step
+ *                of alpha, alpha dx_i dx_j (i<=j: xx xy xz yy yz zz) and
+ *                alpha dx_i dx_j dx_k dx_l (i<=j<=k<=l, lexicographic), dx in um
+ *   alpha_sum  : 1 double, sum over walkers of alpha = exp(-sum t_i / T^(i)) at the end
+ * Errors: RMS_E_CANCELLED, RMS_E_DEVICE, RMS_E_CUDA. */
+rms_status rms_read_signal(rms_run_handle *run, double *S_re, double *S_im, double *moments,
+                           double *alpha_sum);
+
+/* Wait for the run and copy the final per-walker state to host memory (any
+ * pointer may be NULL): i (W*3 int32 unwrapped voxel index), o (W*3 double
+ * offset in [0,1]; the FP32 form's offsets widened), i0 (W*3), o0 (W*3),
+ * c (W int32 label), A (W double exponent of Eq. 5), phase (W*n_shapes*3
+ * double, sum_k dt G_k dx_k in um ms), hash (W uint64, RMS_TRAJ_HASH runs). */
+rms_status rms_read_walkers(rms_run_handle *run, int32_t *i, double *o, int32_t *i0, double *o0, int32_t *c,
+                            double *A, double *phase, uint64_t *hash);
+
+/* Free the run (waits for it first). */
+rms_status rms_destroy_run(rms_run_handle *run);
+
+/* Device time (ms) between the start of the first and the end of the last
+ * step launch of a finished run; synchronises. */
+rms_status rms_run_step_time_ms(rms_run_handle *run, float *ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RMS_H */

@@ -1,0 +1,97 @@
+"""ctypes binding of librms.so (include/rms.h).  Argument marshalling only:
+every step of the simulation runs in the library's CUDA kernels.  There is
+no fallback: if the shared library is missing or fails to load, importing
+this module raises."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librms.so")
+
+RMS_OK = 0
+RMS_W_PROB_RANGE = 1
+RMS_E_INVALID_ARG = -1
+RMS_E_OOM = -2
+RMS_E_CUDA = -3
+RMS_E_STEP_TOO_LARGE = -4
+RMS_E_TIMEOUT = -6
+RMS_E_CANCELLED = -7
+RMS_E_BUSY = -8
+RMS_E_DEVICE = -9
+RMS_E_NOT_READY = -10
+RMS_FP64 = 0
+RMS_FP32 = 1
+RMS_TRAJ_HASH = 1
+
+
+class RmsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"rms status {status}: {msg}")
+        self.status = status
+
+
+class SubstrateDesc(C.Structure):
+    _fields_ = [("labels", C.c_void_p), ("labels_on_device", C.c_int32),
+                ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("voxel_um", C.c_double), ("periodic", C.c_int32 * 3), ("n_labels", C.c_int32),
+                ("D", C.c_void_p), ("T2", C.c_void_p), ("T1", C.c_void_p), ("kappa", C.c_void_p),
+                ("kappa_scalar", C.c_double), ("dead", C.c_void_p), ("stream", C.c_void_p)]
+
+
+class SequenceDesc(C.Structure):
+    _fields_ = [("dt_ms", C.c_double), ("n_steps", C.c_int64), ("n_shapes", C.c_int32), ("G", C.c_void_p),
+                ("mode", C.c_void_p), ("n_dirs", C.c_int32), ("dirs", C.c_void_p), ("n_b", C.c_int32),
+                ("b", C.c_void_p), ("n_rec", C.c_int32), ("rec_steps", C.c_void_p)]
+
+
+class RunDesc(C.Structure):
+    _fields_ = [("n_walkers", C.c_int64), ("walker_begin", C.c_int64), ("seed", C.c_uint64),
+                ("precision", C.c_int32), ("flags", C.c_uint32), ("steps_per_launch", C.c_int32),
+                ("stream", C.c_void_p)]
+
+
+# name -> (argtypes, restype); the exported C entry points of include/rms.h
+SIGNATURES = {
+    "rms_version": ([], C.c_int),
+    "rms_last_error": ([], C.c_char_p),
+    "rms_create_substrate": ([C.POINTER(SubstrateDesc), C.POINTER(C.c_void_p)], C.c_int),
+    "rms_destroy_substrate": ([C.c_void_p], C.c_int),
+    "rms_set_sequence": ([C.c_void_p, C.POINTER(SequenceDesc), C.POINTER(C.c_void_p)], C.c_int),
+    "rms_sequence_bvalues": ([C.c_void_p, C.c_void_p], C.c_int),
+    "rms_destroy_sequence": ([C.c_void_p], C.c_int),
+    "rms_run": ([C.c_void_p, C.POINTER(RunDesc), C.POINTER(C.c_void_p)], C.c_int),
+    "rms_run_query": ([C.c_void_p], C.c_int),
+    "rms_cancel": ([C.c_void_p], C.c_int),
+    "rms_read_signal": ([C.c_void_p] + [C.c_void_p] * 4, C.c_int),
+    "rms_read_walkers": ([C.c_void_p] + [C.c_void_p] * 8, C.c_int),
+    "rms_destroy_run": ([C.c_void_p], C.c_int),
+    "rms_run_step_time_ms": ([C.c_void_p, C.POINTER(C.c_float)], C.c_int),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2012_06478_gb300.build` "
+                          "(there is no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    for name, (args, res) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def last_error() -> str:
+    m = lib.rms_last_error()
+    return m.decode() if m else ""
+
+
+def check(status: int, allow=(RMS_OK,)) -> int:
+    if status not in allow:
+        raise RmsError(status, last_error())
+    return status

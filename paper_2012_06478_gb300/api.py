@@ -1,0 +1,257 @@
+"""Python face of the C ABI, with the same names (argument marshalling only).
+
+    sub = rms_create_substrate(labels, voxel_um, D, T2=..., kappa=..., stream=...)
+    seq = rms_set_sequence(sub, dt_ms, G, dirs, b, rec_steps)
+    run = rms_run(seq, n_walkers, seed, precision=RMS_FP64)
+    S, moments, alpha_sum = rms_read_signal(run)
+
+Inputs may be numpy arrays (host) or, for the label volume, a CUDA tensor
+(device); torch supplies device memory and the stream, nothing else.  The
+handles free their device memory when closed or garbage collected.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence as Seq
+
+import numpy as np
+
+from . import _lib as L
+from ._lib import RMS_FP32, RMS_FP64, RMS_TRAJ_HASH, RmsError, check
+
+__all__ = ["rms_create_substrate", "rms_set_sequence", "rms_run", "rms_read_signal", "rms_read_walkers",
+           "rms_cancel", "rms_run_query", "rms_destroy_run", "rms_destroy_sequence", "rms_destroy_substrate",
+           "rms_sequence_bvalues", "rms_run_step_time_ms", "simulate", "current_stream",
+           "RMS_FP32", "RMS_FP64", "RMS_TRAJ_HASH", "RmsError", "MOMENT_NAMES"]
+
+MOMENT_NAMES = ["1", "xx", "xy", "xz", "yy", "yz", "zz", "xxxx", "xxxy", "xxxz", "xxyy", "xxyz", "xxzz", "xyyy",
+                "xyyz", "xyzz", "xzzz", "yyyy", "yyyz", "yyzz", "yzzz", "zzzz"]
+
+
+def current_stream() -> int:
+    """cudaStream_t of torch's current stream (0 if torch has no CUDA)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return 0
+
+
+def _host(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+class Substrate:
+    def __init__(self, handle, shape_xyz, n_labels, keep=None):
+        self.handle = handle
+        self.shape_xyz = shape_xyz
+        self.n_labels = n_labels
+        self._keep = keep
+
+    def close(self):
+        if self.handle:
+            check(L.lib.rms_destroy_substrate(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Sequence:
+    def __init__(self, handle, sub, n_steps, n_shapes, n_dirs, n_b, n_rec, status):
+        self.handle = handle
+        self.sub = sub
+        self.n_steps, self.n_shapes, self.n_dirs, self.n_b, self.n_rec = n_steps, n_shapes, n_dirs, n_b, n_rec
+        self.status = status
+
+    def close(self):
+        if self.handle:
+            check(L.lib.rms_destroy_sequence(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Run:
+    def __init__(self, handle, seq, n_walkers, precision, flags):
+        self.handle = handle
+        self.seq = seq
+        self.n_walkers = n_walkers
+        self.precision = precision
+        self.flags = flags
+
+    def close(self):
+        if self.handle:
+            check(L.lib.rms_destroy_run(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rms_create_substrate(labels, voxel_um: float, D, T2=None, T1=None, kappa=None, kappa_scalar: float = 0.0,
+                         dead=None, periodic=(1, 1, 1), n_labels: Optional[int] = None,
+                         stream: Optional[int] = None) -> Substrate:
+    """labels: (nz, ny, nx) uint16 numpy array or CUDA tensor (x fastest)."""
+    on_device = hasattr(labels, "is_cuda") and labels.is_cuda
+    if on_device:
+        import torch
+        assert labels.dtype in (torch.uint16, torch.int16) and labels.is_contiguous()
+        nz, ny, nx = labels.shape
+        lab_ptr = labels.data_ptr()
+        keep_lab = labels
+    else:
+        lab = np.ascontiguousarray(labels, dtype=np.uint16)
+        nz, ny, nx = lab.shape
+        lab_ptr = lab.ctypes.data
+        keep_lab = lab
+    Dv = _host(D, np.float64)
+    Lc = int(n_labels if n_labels is not None else Dv.size)
+    T2v, T1v = _host(T2, np.float64), _host(T1, np.float64)
+    Kv = _host(kappa, np.float64)
+    deadv = _host(dead, np.uint8)
+    d = L.SubstrateDesc()
+    d.labels = lab_ptr
+    d.labels_on_device = 1 if on_device else 0
+    d.nx, d.ny, d.nz = nx, ny, nz
+    d.voxel_um = float(voxel_um)
+    d.periodic = (C.c_int32 * 3)(*[int(p) for p in periodic])
+    d.n_labels = Lc
+    d.D, d.T2, d.T1, d.kappa = _ptr(Dv), _ptr(T2v), _ptr(T1v), _ptr(Kv)
+    d.kappa_scalar = float(kappa_scalar)
+    d.dead = _ptr(deadv)
+    d.stream = current_stream() if stream is None else stream
+    h = C.c_void_p()
+    check(L.lib.rms_create_substrate(C.byref(d), C.byref(h)))
+    return Substrate(h, (nx, ny, nz), Lc, keep=None if not on_device else keep_lab)
+
+
+def rms_set_sequence(sub: Substrate, dt_ms: float, G, dirs, b, rec_steps: Seq[int] = (), mode=None) -> Sequence:
+    Gv = np.ascontiguousarray(np.atleast_2d(np.asarray(G, np.float64)))
+    S, N = Gv.shape
+    dv = np.ascontiguousarray(np.asarray(dirs, np.float64).reshape(-1, 3))
+    bv = np.ascontiguousarray(np.asarray(b, np.float64).ravel())
+    rv = np.ascontiguousarray(np.asarray(rec_steps, np.int64).ravel())
+    mv = _host(mode, np.uint8)
+    d = L.SequenceDesc()
+    d.dt_ms = float(dt_ms)
+    d.n_steps = N
+    d.n_shapes = S
+    d.G = Gv.ctypes.data if N else None
+    d.mode = _ptr(mv)
+    d.n_dirs = dv.shape[0]
+    d.dirs = dv.ctypes.data
+    d.n_b = bv.size
+    d.b = bv.ctypes.data
+    d.n_rec = rv.size
+    d.rec_steps = rv.ctypes.data if rv.size else None
+    h = C.c_void_p()
+    st = check(L.lib.rms_set_sequence(sub.handle, C.byref(d), C.byref(h)), allow=(L.RMS_OK, L.RMS_W_PROB_RANGE))
+    return Sequence(h, sub, N, S, dv.shape[0], bv.size, rv.size, st)
+
+
+def rms_sequence_bvalues(seq: Sequence) -> np.ndarray:
+    out = np.zeros(seq.n_shapes)
+    check(L.lib.rms_sequence_bvalues(seq.handle, out.ctypes.data))
+    return out
+
+
+def rms_run(seq: Sequence, n_walkers: int, seed: int, precision: int = RMS_FP64, flags: int = 0,
+            walker_begin: int = 0, steps_per_launch: int = 0, stream: Optional[int] = None) -> Run:
+    d = L.RunDesc()
+    d.n_walkers = int(n_walkers)
+    d.walker_begin = int(walker_begin)
+    d.seed = int(seed)
+    d.precision = int(precision)
+    d.flags = int(flags)
+    d.steps_per_launch = int(steps_per_launch)
+    d.stream = current_stream() if stream is None else stream
+    h = C.c_void_p()
+    check(L.lib.rms_run(seq.handle, C.byref(d), C.byref(h)))
+    return Run(h, seq, int(n_walkers), precision, flags)
+
+
+def rms_run_query(run: Run) -> bool:
+    """True when finished."""
+    return check(L.lib.rms_run_query(run.handle), allow=(L.RMS_OK, L.RMS_E_NOT_READY)) == L.RMS_OK
+
+
+def rms_cancel(run: Run) -> None:
+    check(L.lib.rms_cancel(run.handle))
+
+
+def rms_read_signal(run: Run):
+    """(S complex (n_shapes, n_dirs, n_b), moments (n_rec, 22), alpha_sum)."""
+    q = run.seq
+    n = q.n_shapes * q.n_dirs * q.n_b
+    re, im = np.zeros(n), np.zeros(n)
+    mom = np.zeros((q.n_rec, 22))
+    asum = np.zeros(1)
+    check(L.lib.rms_read_signal(run.handle, re.ctypes.data, im.ctypes.data, mom.ctypes.data if q.n_rec else None,
+                                asum.ctypes.data))
+    return (re + 1j * im).reshape(q.n_shapes, q.n_dirs, q.n_b), mom, float(asum[0])
+
+
+def rms_read_walkers(run: Run) -> dict:
+    W, S = run.n_walkers, run.seq.n_shapes
+    out = dict(i=np.zeros((W, 3), np.int32), o=np.zeros((W, 3)), i0=np.zeros((W, 3), np.int32),
+               o0=np.zeros((W, 3)), c=np.zeros(W, np.int32), A=np.zeros(W), phase=np.zeros((W, S, 3)),
+               hash=np.zeros(W, np.uint64))
+    check(L.lib.rms_read_walkers(run.handle, *[out[k].ctypes.data for k in
+                                               ("i", "o", "i0", "o0", "c", "A", "phase", "hash")]))
+    return out
+
+
+def rms_run_step_time_ms(run: Run) -> float:
+    ms = C.c_float()
+    check(L.lib.rms_run_step_time_ms(run.handle, C.byref(ms)))
+    return float(ms.value)
+
+
+def rms_destroy_run(run: Run) -> None:
+    run.close()
+
+
+def rms_destroy_sequence(seq: Sequence) -> None:
+    seq.close()
+
+
+def rms_destroy_substrate(sub: Substrate) -> None:
+    sub.close()
+
+
+def simulate(wl, precision: int = RMS_FP64, n_walkers: Optional[int] = None, seed: Optional[int] = None,
+             hash_: bool = False, walker_begin: int = 0, steps_per_launch: int = 0, walkers: bool = False,
+             stream: Optional[int] = None) -> dict:
+    """Run one workload (an rms_inputs.Workload) end to end through the C ABI."""
+    sub = rms_create_substrate(wl.labels, wl.voxel_um, wl.D, T2=wl.T2, T1=wl.T1, kappa=wl.kappa, dead=wl.dead,
+                               periodic=wl.periodic, stream=stream)
+    G = np.asarray(wl.G, np.float64)
+    G = G.reshape(-1, wl.n_steps) if wl.n_steps else np.zeros((G.shape[0] if G.ndim == 2 else 1, 0))
+    seq = rms_set_sequence(sub, wl.dt, G, wl.dirs, wl.b, wl.rec_steps, mode=wl.mode)
+    run = rms_run(seq, wl.n_walkers if n_walkers is None else n_walkers, wl.seed if seed is None else seed,
+                  precision, RMS_TRAJ_HASH if hash_ else 0, walker_begin, steps_per_launch, stream)
+    S, mom, asum = rms_read_signal(run)
+    res = dict(S=S, moments=mom, alpha_sum=asum, status=seq.status, step_ms=rms_run_step_time_ms(run))
+    if walkers:
+        res.update(rms_read_walkers(run))
+    run.close()
+    seq.close()
+    sub.close()
+    return res

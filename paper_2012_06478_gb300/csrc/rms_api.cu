@@ -1,0 +1,977 @@
+// rms_api.cu -- the C ABI (include/rms.h): substrate, sequence and run
+// handles, the set-up kernels that build the per-label and per-pair tables,
+// walker initialisation, the moment and signal reductions and the read-out.
+//
+// Built with -fmad=false: the tables (step lengths, relaxation rates,
+// permeation thresholds, waveform weights) and the read-out are evaluated
+// with the same separately rounded FP64 operations as the CPU reference.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rms.h"
+#include "rms_device.cuh"
+#include "rms_internal.h"
+
+using namespace rms;
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_last_error;
+
+static rms_status fail(rms_status st, const std::string &msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+#define RMS_CUDA(call)                                                                            \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(e_ == cudaErrorMemoryAllocation ? RMS_E_OOM : RMS_E_CUDA,                 \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+    } while (0)
+
+extern "C" int rms_version(void) { return 10000; }
+extern "C" const char *rms_last_error(void) { return g_last_error.c_str(); }
+
+// ------------------------------------------------------------------ handles
+
+struct rms_substrate {
+    int device = 0;
+    int32_t nx = 0, ny = 0, nz = 0;
+    double voxel_um = 0;
+    int32_t periodic[3] = {1, 1, 1};
+    int32_t L = 0;
+    std::vector<double> D, T2, T1, kappa;
+    std::vector<uint8_t> dead;
+    uint16_t *d_labels = nullptr;
+    double *d_D = nullptr, *d_T2 = nullptr, *d_T1 = nullptr, *d_kappa = nullptr;
+    uint8_t *d_dead = nullptr;
+    int32_t *d_ok = nullptr;  // raster list of non-dead voxels (nullptr: none dead)
+    int64_t n_ok = 0;
+    std::atomic<int> refs{0};
+};
+
+struct rms_sequence {
+    rms_substrate *sub = nullptr;
+    double dt = 0;
+    int64_t n_steps = 0;
+    int32_t S = 0, n_dirs = 0, n_b = 0, n_rec = 0;
+    int32_t any_relax = 0;
+    int32_t has_mode = 0;
+    double *d_s64 = nullptr, *d_dtR64 = nullptr, *d_wG64 = nullptr;
+    float *d_s32 = nullptr, *d_dtR32 = nullptr, *d_wG32 = nullptr;
+    uint32_t *d_T = nullptr;
+    uint8_t *d_flags = nullptr, *d_mode = nullptr;
+    int32_t *d_rec_of = nullptr;
+    double *d_dirs = nullptr, *d_b = nullptr, *d_bs = nullptr, *d_q = nullptr;
+    std::atomic<int> refs{0};
+};
+
+struct rms_run_handle {
+    rms_sequence *seq = nullptr;
+    int64_t W = 0, w_begin = 0;
+    uint64_t seed = 0;
+    int32_t precision = RMS_FP64;
+    uint32_t flags = 0;
+    cudaStream_t stream = nullptr;
+    int32_t n_blocks = 0;
+    char *d_state = nullptr;  // one allocation for the walker state
+    WalkerState<double> st64{};
+    WalkerState<float> st32{};
+    double *d_mom_partial = nullptr, *d_mom = nullptr;
+    double *d_ro_partial = nullptr, *d_S = nullptr;  // S: [combo][2] + alpha sum
+    int32_t *d_status = nullptr;
+    int32_t *h_cancel = nullptr, *d_cancel = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_end = nullptr;
+    int32_t n_combo = 0, n_chunks = 0;
+};
+
+// ------------------------------------------------------------------ set-up kernels
+
+__global__ void max_label_kernel(const uint16_t *lab, int64_t n, uint32_t *out)
+{
+    uint32_t m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (uint32_t)lab[i]);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// Raster list of the voxels whose label is not dead (Sec. 2.2 item 1):
+// per-block counts, one scan, then an ordered fill.
+constexpr int kOkBlock = 1024;
+
+__global__ void ok_count_kernel(const uint16_t *lab, int64_t n, const uint8_t *dead, int32_t *cnt)
+{
+    __shared__ int32_t s;
+    if (threadIdx.x == 0) s = 0;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * kOkBlock + threadIdx.x;
+    const int ok = i < n && !dead[lab[i]];
+    const int wc = __popc(__ballot_sync(0xffffffffu, ok));
+    if ((threadIdx.x & 31) == 0 && wc) atomicAdd(&s, wc);
+    __syncthreads();
+    if (threadIdx.x == 0) cnt[blockIdx.x] = s;
+}
+
+__global__ void exclusive_scan_kernel(int32_t *cnt, int64_t n, int64_t *total)
+{
+    // single block; serial over chunks of blockDim.x, each chunk scanned in shared memory
+    __shared__ int64_t buf[1024];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const int64_t x = i < n ? cnt[i] : 0;
+        buf[threadIdx.x] = x;
+        __syncthreads();
+        for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+            const int64_t y = threadIdx.x >= (unsigned)off ? buf[threadIdx.x - off] : 0;
+            __syncthreads();
+            buf[threadIdx.x] += y;
+            __syncthreads();
+        }
+        if (i < n) cnt[i] = (int32_t)(carry + buf[threadIdx.x] - x);
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += buf[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void ok_fill_kernel(const uint16_t *lab, int64_t n, const uint8_t *dead, const int32_t *start,
+                               int32_t *list)
+{
+    __shared__ int32_t warp_base[kOkBlock / 32];
+    const int64_t i = (int64_t)blockIdx.x * kOkBlock + threadIdx.x;
+    const int ok = i < n && !dead[lab[i]];
+    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_base[wid] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t acc = 0;
+        for (int k = 0; k < kOkBlock / 32; ++k) {
+            const int32_t c = warp_base[k];
+            warp_base[k] = acc;
+            acc += c;
+        }
+    }
+    __syncthreads();
+    if (ok) list[start[blockIdx.x] + warp_base[wid] + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
+}
+
+// Eq. 1 (d = 3): ds = sqrt((6 D) dt); s = ds / l_p.  Eq. 5: dt / T per label.
+__global__ void label_tables_kernel(int32_t L, const double *D, const double *T2, const double *T1, double dt,
+                                    double voxel, double *s64, float *s32, double *dtR64, float *dtR32)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L) return;
+    const double ds = sqrt((6.0 * D[c]) * dt);
+    const double s = ds / voxel;
+    s64[c] = s;
+    s32[c] = (float)s;
+    const double r2 = isinf(T2[c]) ? 0.0 : dt / T2[c];
+    const double r1 = isinf(T1[c]) ? 0.0 : dt / T1[c];
+    dtR64[c] = r2;
+    dtR64[L + c] = r1;
+    dtR64[2 * L + c] = 0.0;
+    dtR32[c] = (float)r2;
+    dtR32[L + c] = (float)r1;
+    dtR32[2 * L + c] = 0.0f;
+}
+
+// Eq. 3: P_{1->2} = (kappa ds1 C / D1) / (1 + (kappa/2)(ds1/D1 + ds2/D2) C),
+// C = C_3 = 2/3 (Eq. 2b), evaluated as ((kappa ds1)/D1) C over
+// 1 + ((kappa/2)((ds1/D1) + (ds2/D2))) C.  The walker crosses when a uniform
+// 32-bit word is below T = min(floor(P 2^32), 2^32 - 1).
+__global__ void pair_tables_kernel(int32_t L, const double *D, const double *kappa, const uint8_t *dead,
+                                   double dt, uint32_t *T, int32_t *warn)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)L * L) return;
+    const int a = (int)(idx / L), b = (int)(idx % L);
+    const double k = kappa[idx];
+    uint32_t thr = 0u;
+    if (a != b && !dead[a] && !dead[b] && k > 0.0) {
+        const double C = 2.0 / 3.0;
+        const double ds1 = sqrt((6.0 * D[a]) * dt);
+        const double ds2 = sqrt((6.0 * D[b]) * dt);
+        const double num = ((k * ds1) / D[a]) * C;
+        const double den = 1.0 + ((k / 2.0) * ((ds1 / D[a]) + (ds2 / D[b]))) * C;
+        const double P = num / den;
+        if (P > 1.0) atomicOr(warn, 1);
+        if (P >= 1.0) {
+            thr = 0xFFFFFFFFu;
+        } else if (P > 0.0) {
+            const double x = floor(P * 4294967296.0);
+            thr = x >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)x;
+        }
+    }
+    T[idx] = thr;
+}
+
+// Per step: weights dt G_{s,k}, the step flags and the recording index.
+__global__ void step_tables_kernel(int64_t N, int32_t S, double dt, const double *G, const int64_t *rec,
+                                   int32_t n_rec, double *wG64, float *wG32, uint8_t *flags, int32_t *rec_of)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // 0-based step index
+    if (k >= N) return;
+    uint8_t f = 0;
+    for (int s = 0; s < S; ++s) {
+        const double w = dt * G[(int64_t)s * N + k];
+        wG64[(int64_t)s * N + k] = w;
+        wG32[(int64_t)s * N + k] = (float)w;
+        if (w != 0.0) f |= 1u;
+    }
+    // binary search of step k+1 among the recording steps
+    int lo = 0, hi = n_rec;
+    while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (rec[mid] < k + 1)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    int32_t r = -1;
+    if (lo < n_rec && rec[lo] == k + 1) {
+        r = lo;
+        f |= 2u;
+    }
+    flags[k] = f;
+    rec_of[k] = r;
+}
+
+__device__ __forceinline__ void neumaier(double &sum, double &comp, double x)
+{
+    const double t = sum + x;
+    if (fabs(sum) >= fabs(x))
+        comp += (sum - t) + x;
+    else
+        comp += (x - t) + sum;
+    sum = t;
+}
+
+// b of a unit waveform: b_s = dt sum_{j=1..N} F_{j-1}^2, F_j = F_{j-1} + dt G_j
+// (compensated sum); then q = sqrt(b / b_s), the amplitude giving b.
+__global__ void bvalue_kernel(int64_t N, int32_t S, double dt, const double *G, int32_t n_b, const double *b,
+                              double *bs_out, double *q)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    double F = 0.0, sum = 0.0, comp = 0.0;
+    for (int64_t j = 1; j <= N; ++j) {
+        neumaier(sum, comp, F * F);
+        F = F + dt * G[(int64_t)s * N + (j - 1)];
+    }
+    const double bs = dt * (sum + comp);
+    bs_out[s] = bs;
+    for (int i = 0; i < n_b; ++i) q[s * n_b + i] = bs > 0.0 ? sqrt(b[i] / bs) : 0.0;
+}
+
+// ------------------------------------------------------------------ init (Sec. 2.2 item 1)
+
+template <typename Real>
+__global__ void init_kernel(Geometry g, const int32_t *ok_list, int64_t n_ok, WalkerState<Real> st,
+                            RunCtl ctl, bool hash)
+{
+    const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= ctl.n_walkers) return;
+    const uint64_t w = (uint64_t)(ctl.w_begin + li);
+    const U4 x = draw(ctl.seed, w, 0u, kTagInit, 0u);
+    const U4 y = draw(ctl.seed, w, 0u, kTagInit, 1u);
+    const uint64_t r = ((uint64_t)x.x << 32) | (uint64_t)x.y;
+    const int64_t idx = (int64_t)__umul64hi(r, (uint64_t)n_ok);
+    const int64_t vox = ok_list ? (int64_t)ok_list[idx] : idx;
+    const int32_t ix = (int32_t)(vox % g.nx);
+    const int32_t iy = (int32_t)((vox / g.nx) % g.ny);
+    const int32_t iz = (int32_t)(vox / ((int64_t)g.nx * g.ny));
+    const double o[3] = {u01(x.z), u01(x.w), u01(y.x)};
+    const int32_t i0[3] = {ix, iy, iz};
+    for (int a = 0; a < 3; ++a) {
+        st.o[a][li] = (Real)o[a];
+        st.o0[a][li] = (Real)o[a];
+        st.i0[a][li] = i0[a];
+        st.di[a][li] = 0;
+    }
+    st.c[li] = g.labels[vox];
+    st.A[li] = Real(0);
+    if (st.A_c) st.A_c[li] = Real(0);
+    for (int k = 0; k < ctl.n_shapes * 3; ++k) {
+        st.phase[(int64_t)k * ctl.n_walkers + li] = Real(0);
+        if (st.phase_c) st.phase_c[(int64_t)k * ctl.n_walkers + li] = Real(0);
+    }
+    if (hash) st.hash[li] = 0ull;
+}
+
+// ------------------------------------------------------------------ reductions
+
+// Moments: fixed-order compensated sum of the per-block partials.
+__global__ void moments_reduce_kernel(const double *part, int32_t n_rec, int32_t n_blocks, double *out)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_rec * kMoments) return;
+    const int r = idx / kMoments, m = idx % kMoments;
+    double s = 0.0, c = 0.0;
+    for (int b = 0; b < n_blocks; ++b) neumaier(s, c, part[((int64_t)r * n_blocks + b) * kMoments + m]);
+    out[idx] = s + c;
+}
+
+// Read-out (Eq. 7): for every (shape, direction, b) combination the sums of
+// alpha cos(phi) and -alpha sin(phi) over a chunk of walkers, phi = q (g . Phi_s),
+// alpha = exp(-A).  One thread per combination; the walkers of the chunk are
+// staged through shared memory in tiles.  The extra combination n_combo
+// carries the sum of alpha.
+constexpr int kRoBlock = 128;
+constexpr int kRoTile = 64;
+constexpr int64_t kRoChunk = 4096;
+
+template <typename Real>
+__global__ void __launch_bounds__(kRoBlock)
+readout_kernel(const Real *phase, const Real *phase_c, const Real *A, const Real *A_c, int64_t W, int32_t S,
+               const double *q, const double *dirs, int32_t n_dirs, int32_t n_b, int32_t n_combo,
+               double *part)
+{
+    __shared__ double sP[kRoTile][kMaxShapes * 3];
+    __shared__ double sAl[kRoTile];
+    const int combo = blockIdx.x * kRoBlock + threadIdx.x;
+    int s = 0;
+    double qq = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    if (combo < n_combo) {
+        const int ib = combo % n_b;
+        const int gi = (combo / n_b) % n_dirs;
+        s = combo / (n_b * n_dirs);
+        qq = q[s * n_b + ib];
+        g0 = dirs[3 * gi];
+        g1 = dirs[3 * gi + 1];
+        g2 = dirs[3 * gi + 2];
+    }
+    const int64_t w0 = (int64_t)blockIdx.y * kRoChunk;
+    const int64_t w1 = min(W, w0 + kRoChunk);
+    double re = 0.0, im = 0.0;
+    for (int64_t base = w0; base < w1; base += kRoTile) {
+        const int nt = (int)min((int64_t)kRoTile, w1 - base);
+        for (int e = threadIdx.x; e < nt * (S * 3 + 1); e += kRoBlock) {
+            const int j = e % nt, k = e / nt;
+            const int64_t w = base + j;
+            if (k < S * 3) {
+                double p = (double)phase[(int64_t)k * W + w];
+                if (phase_c) p = p - (double)phase_c[(int64_t)k * W + w];
+                sP[j][k] = p;
+            } else {
+                double a = (double)A[w];
+                if (A_c) a = a - (double)A_c[w];
+                sAl[j] = exp(-a);
+            }
+        }
+        __syncthreads();
+        if (combo < n_combo) {
+            for (int j = 0; j < nt; ++j) {
+                const double phi = qq * (g0 * sP[j][3 * s] + g1 * sP[j][3 * s + 1] + g2 * sP[j][3 * s + 2]);
+                double sn, cs;
+                sincos(phi, &sn, &cs);
+                re += sAl[j] * cs;
+                im += -(sAl[j] * sn);
+            }
+        } else if (combo == n_combo) {
+            for (int j = 0; j < nt; ++j) re += sAl[j];
+        }
+        __syncthreads();
+    }
+    if (combo <= n_combo) {
+        part[((int64_t)blockIdx.y * (n_combo + 1) + combo) * 2 + 0] = re;
+        part[((int64_t)blockIdx.y * (n_combo + 1) + combo) * 2 + 1] = im;
+    }
+}
+
+__global__ void readout_reduce_kernel(const double *part, int32_t n_chunks, int32_t n_combo, double *out)
+{
+    const int combo = blockIdx.x * blockDim.x + threadIdx.x;
+    if (combo > n_combo) return;
+    double rs = 0, rc = 0, is = 0, ic = 0;
+    for (int k = 0; k < n_chunks; ++k) {
+        neumaier(rs, rc, part[((int64_t)k * (n_combo + 1) + combo) * 2 + 0]);
+        neumaier(is, ic, part[((int64_t)k * (n_combo + 1) + combo) * 2 + 1]);
+    }
+    out[combo * 2 + 0] = rs + rc;
+    out[combo * 2 + 1] = is + ic;
+}
+
+__global__ void normalise_kernel(double *S, int32_t n_combo)
+{
+    const int combo = blockIdx.x * blockDim.x + threadIdx.x;
+    if (combo >= n_combo) return;
+    const double asum = S[n_combo * 2];
+    S[combo * 2 + 0] = S[combo * 2 + 0] / asum;
+    S[combo * 2 + 1] = S[combo * 2 + 1] / asum;
+}
+
+// Final per-walker state in array-of-structures form, FP64.
+template <typename Real>
+__global__ void export_kernel(WalkerState<Real> st, int64_t W, int32_t S, bool hash, int32_t *i, double *o,
+                              int32_t *i0, double *o0, int32_t *c, double *A, double *phase, uint64_t *h)
+{
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    for (int a = 0; a < 3; ++a) {
+        i[3 * w + a] = st.i0[a][w] + st.di[a][w];
+        o[3 * w + a] = (double)st.o[a][w];
+        i0[3 * w + a] = st.i0[a][w];
+        o0[3 * w + a] = (double)st.o0[a][w];
+    }
+    c[w] = st.c[w];
+    A[w] = st.A_c ? (double)st.A[w] - (double)st.A_c[w] : (double)st.A[w];
+    for (int k = 0; k < S * 3; ++k) {
+        double p = (double)st.phase[(int64_t)k * W + w];
+        if (st.phase_c) p = p - (double)st.phase_c[(int64_t)k * W + w];
+        phase[(int64_t)w * S * 3 + k] = p;
+    }
+    h[w] = hash ? st.hash[w] : 0ull;
+}
+
+// ------------------------------------------------------------------ substrate
+
+template <typename T>
+static rms_status upload(T **dst, const T *src, size_t n, cudaStream_t s, bool src_on_device = false)
+{
+    RMS_CUDA(cudaMallocAsync((void **)dst, sizeof(T) * (n ? n : 1), s));
+    if (n)
+        RMS_CUDA(cudaMemcpyAsync(*dst, src, sizeof(T) * n,
+                                 src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    return RMS_OK;
+}
+
+#define RMS_TRY(expr)                 \
+    do {                              \
+        rms_status st_ = (expr);      \
+        if (st_ < 0) return st_;      \
+    } while (0)
+
+static void free_substrate(rms_substrate *s, cudaStream_t st)
+{
+    cudaFreeAsync(s->d_labels, st);
+    cudaFreeAsync(s->d_D, st);
+    cudaFreeAsync(s->d_T2, st);
+    cudaFreeAsync(s->d_T1, st);
+    cudaFreeAsync(s->d_kappa, st);
+    cudaFreeAsync(s->d_dead, st);
+    if (s->d_ok) cudaFreeAsync(s->d_ok, st);
+}
+
+static rms_status create_substrate_impl(const rms_substrate_desc *d, rms_substrate *s)
+{
+    cudaStream_t st = (cudaStream_t)d->stream;
+    const int64_t nvox = (int64_t)d->nx * d->ny * d->nz;
+    const int L = d->n_labels;
+    s->nx = d->nx;
+    s->ny = d->ny;
+    s->nz = d->nz;
+    s->voxel_um = d->voxel_um;
+    for (int a = 0; a < 3; ++a) s->periodic[a] = d->periodic[a] ? 1 : 0;
+    s->L = L;
+    s->D.assign(d->D, d->D + L);
+    s->T2.assign(L, INFINITY);
+    s->T1.assign(L, INFINITY);
+    if (d->T2) s->T2.assign(d->T2, d->T2 + L);
+    if (d->T1) s->T1.assign(d->T1, d->T1 + L);
+    if (d->kappa)
+        s->kappa.assign(d->kappa, d->kappa + (size_t)L * L);
+    else
+        s->kappa.assign((size_t)L * L, d->kappa_scalar);
+    s->dead.assign(L, 0);
+    if (d->dead)
+        for (int c = 0; c < L; ++c) s->dead[c] = d->dead[c] ? 1 : 0;
+    for (int c = 0; c < L; ++c) {
+        if (!(s->D[c] > 0.0) || !std::isfinite(s->D[c]))
+            return fail(RMS_E_INVALID_ARG, "D must be finite and > 0 for every label");
+        if (!(s->T2[c] > 0.0) || !(s->T1[c] > 0.0))
+            return fail(RMS_E_INVALID_ARG, "T1 and T2 must be > 0 (INFINITY for none)");
+    }
+    for (size_t k = 0; k < s->kappa.size(); ++k)
+        if (!(s->kappa[k] >= 0.0) || !std::isfinite(s->kappa[k]))
+            return fail(RMS_E_INVALID_ARG, "kappa must be finite and >= 0");
+    RMS_TRY(upload(&s->d_labels, d->labels, (size_t)nvox, st, d->labels_on_device != 0));
+    RMS_TRY(upload(&s->d_D, s->D.data(), L, st));
+    RMS_TRY(upload(&s->d_T2, s->T2.data(), L, st));
+    RMS_TRY(upload(&s->d_T1, s->T1.data(), L, st));
+    RMS_TRY(upload(&s->d_kappa, s->kappa.data(), (size_t)L * L, st));
+    RMS_TRY(upload(&s->d_dead, s->dead.data(), L, st));
+    // every label must be < L
+    uint32_t *d_max = nullptr;
+    RMS_CUDA(cudaMallocAsync((void **)&d_max, sizeof(uint32_t), st));
+    RMS_CUDA(cudaMemsetAsync(d_max, 0, sizeof(uint32_t), st));
+    max_label_kernel<<<1024, 256, 0, st>>>(s->d_labels, nvox, d_max);
+    RMS_CUDA(cudaGetLastError());
+    uint32_t mx = 0;
+    RMS_CUDA(cudaMemcpyAsync(&mx, d_max, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    RMS_CUDA(cudaFreeAsync(d_max, st));
+    RMS_CUDA(cudaStreamSynchronize(st));
+    if ((int64_t)mx >= L) return fail(RMS_E_INVALID_ARG, "a label value is >= n_labels");
+    bool any_dead = false;
+    for (int c = 0; c < L; ++c) any_dead |= s->dead[c] != 0;
+    if (!any_dead) {
+        s->n_ok = nvox;
+    } else {
+        const int64_t nblk = (nvox + kOkBlock - 1) / kOkBlock;
+        int32_t *d_cnt = nullptr;
+        int64_t *d_tot = nullptr;
+        RMS_CUDA(cudaMallocAsync((void **)&d_cnt, sizeof(int32_t) * nblk, st));
+        RMS_CUDA(cudaMallocAsync((void **)&d_tot, sizeof(int64_t), st));
+        ok_count_kernel<<<(unsigned)nblk, kOkBlock, 0, st>>>(s->d_labels, nvox, s->d_dead, d_cnt);
+        exclusive_scan_kernel<<<1, 1024, 0, st>>>(d_cnt, nblk, d_tot);
+        int64_t tot = 0;
+        RMS_CUDA(cudaMemcpyAsync(&tot, d_tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        RMS_CUDA(cudaStreamSynchronize(st));
+        if (tot == 0) {
+            cudaFreeAsync(d_cnt, st);
+            cudaFreeAsync(d_tot, st);
+            return fail(RMS_E_INVALID_ARG, "every voxel is dead");
+        }
+        RMS_CUDA(cudaMallocAsync((void **)&s->d_ok, sizeof(int32_t) * tot, st));
+        ok_fill_kernel<<<(unsigned)nblk, kOkBlock, 0, st>>>(s->d_labels, nvox, s->d_dead, d_cnt, s->d_ok);
+        RMS_CUDA(cudaGetLastError());
+        RMS_CUDA(cudaFreeAsync(d_cnt, st));
+        RMS_CUDA(cudaFreeAsync(d_tot, st));
+        s->n_ok = tot;
+    }
+    RMS_CUDA(cudaStreamSynchronize(st));
+    return RMS_OK;
+}
+
+extern "C" rms_status rms_create_substrate(const rms_substrate_desc *d, rms_substrate **out)
+{
+    if (!d || !out || !d->labels || !d->D) return fail(RMS_E_INVALID_ARG, "null descriptor field");
+    *out = nullptr;
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1 || (int64_t)d->nx * d->ny * d->nz >= (1ll << 31))
+        return fail(RMS_E_INVALID_ARG, "grid size out of range");
+    if (!(d->voxel_um > 0.0) || !std::isfinite(d->voxel_um)) return fail(RMS_E_INVALID_ARG, "voxel_um must be > 0");
+    if (d->n_labels < 1 || d->n_labels > 65536) return fail(RMS_E_INVALID_ARG, "n_labels out of range");
+    rms_substrate *s = new (std::nothrow) rms_substrate();
+    if (!s) return fail(RMS_E_OOM, "host allocation");
+    cudaGetDevice(&s->device);
+    rms_status r = create_substrate_impl(d, s);
+    if (r < 0) {
+        free_substrate(s, (cudaStream_t)d->stream);
+        cudaStreamSynchronize((cudaStream_t)d->stream);
+        delete s;
+        return r;
+    }
+    *out = s;
+    return RMS_OK;
+}
+
+extern "C" rms_status rms_destroy_substrate(rms_substrate *s)
+{
+    if (!s) return RMS_OK;
+    if (s->refs.load() > 0) return fail(RMS_E_BUSY, "substrate still used by a sequence");
+    cudaDeviceSynchronize();
+    free_substrate(s, 0);
+    cudaStreamSynchronize(0);
+    delete s;
+    return RMS_OK;
+}
+
+// ------------------------------------------------------------------ sequence
+
+static void free_sequence(rms_sequence *q, cudaStream_t st)
+{
+    void *p[] = {q->d_s64, q->d_dtR64, q->d_wG64, q->d_s32, q->d_dtR32, q->d_wG32, q->d_T, q->d_flags,
+                 q->d_mode, q->d_rec_of, q->d_dirs, q->d_b, q->d_bs, q->d_q};
+    for (void *x : p)
+        if (x) cudaFreeAsync(x, st);
+}
+
+static rms_status set_sequence_impl(rms_substrate *sub, const rms_sequence_desc *d, rms_sequence *q,
+                                    bool *warn)
+{
+    cudaStream_t st = 0;
+    const int L = sub->L;
+    const int64_t N = d->n_steps;
+    const int S = d->n_shapes;
+    q->sub = sub;
+    q->dt = d->dt_ms;
+    q->n_steps = N;
+    q->S = S;
+    q->n_dirs = d->n_dirs;
+    q->n_b = d->n_b;
+    q->n_rec = d->n_rec;
+    for (int c = 0; c < L; ++c) {
+        if (sub->dead[c]) continue;
+        if (std::sqrt((6.0 * sub->D[c]) * d->dt_ms) >= sub->voxel_um)
+            return fail(RMS_E_STEP_TOO_LARGE, "step length sqrt(6 D dt) >= voxel size for label " + std::to_string(c));
+        if (!std::isinf(sub->T2[c]) || !std::isinf(sub->T1[c])) q->any_relax = 1;
+    }
+    for (int i = 0; i < d->n_rec; ++i) {
+        if (d->rec_steps[i] < 1 || d->rec_steps[i] > N || (i > 0 && d->rec_steps[i] <= d->rec_steps[i - 1]))
+            return fail(RMS_E_INVALID_ARG, "rec_steps must be strictly increasing in [1, n_steps]");
+    }
+    for (int i = 0; i < d->n_b; ++i)
+        if (!(d->b[i] >= 0.0)) return fail(RMS_E_INVALID_ARG, "b-values must be >= 0");
+    if (d->mode)
+        for (int64_t k = 0; k < N; ++k)
+            if (d->mode[k] > 2) return fail(RMS_E_INVALID_ARG, "mode values are 0, 1 or 2");
+    RMS_CUDA(cudaMallocAsync((void **)&q->d_s64, sizeof(double) * L, st));
+    RMS_CUDA(cudaMallocAsync((void **)&q->d_s32, sizeof(float) * L, st));
+    RMS_CUDA(cudaMallocAsync((void **)&q->d_dtR64, sizeof(double) * 3 * L, st));
+    RMS_CUDA(cudaMallocAsync((void **)&q->d_dtR32, sizeof(float) * 3 * L, st));
+    RMS_CUDA(cudaMallocAsync((void **)&q->d_T, sizeof(uint32_t) * (size_t)L * L, st));
+    const size_t nG = (size_t)S * (N ? N : 1);
+    RMS_CUDA(cudaMallocAsync((void **)&q->d_wG64, sizeof(double) * nG, st));
+    RMS_CUDA(cudaMallocAsync((void **)&q->d_wG32, sizeof(float) * nG, st));
+    RMS_CUDA(cudaMallocAsync((void **)&q->d_flags, N ? N : 1, st));
+    RMS_CUDA(cudaMallocAsync((void **)&q->d_rec_of, sizeof(int32_t) * (N ? N : 1), st));
+    if (d->mode) {
+        RMS_TRY(upload(&q->d_mode, d->mode, (size_t)N, st));
+        q->has_mode = 1;
+    }
+    RMS_TRY(upload(&q->d_dirs, d->dirs, (size_t)3 * d->n_dirs, st));
+    RMS_TRY(upload(&q->d_b, d->b, (size_t)d->n_b, st));
+    RMS_CUDA(cudaMallocAsync((void **)&q->d_bs, sizeof(double) * S, st));
+    RMS_CUDA(cudaMallocAsync((void **)&q->d_q, sizeof(double) * S * d->n_b, st));
+    double *d_G = nullptr;
+    int64_t *d_rec = nullptr;
+    int32_t *d_warn = nullptr;
+    RMS_TRY(upload(&d_G, d->G, (size_t)S * N, st));
+    RMS_TRY(upload(&d_rec, d->rec_steps, (size_t)d->n_rec, st));
+    RMS_CUDA(cudaMallocAsync((void **)&d_warn, sizeof(int32_t), st));
+    RMS_CUDA(cudaMemsetAsync(d_warn, 0, sizeof(int32_t), st));
+    label_tables_kernel<<<(L + 127) / 128, 128, 0, st>>>(L, sub->d_D, sub->d_T2, sub->d_T1, d->dt_ms, sub->voxel_um,
+                                                           q->d_s64, q->d_s32, q->d_dtR64, q->d_dtR32);
+    const int64_t LL = (int64_t)L * L;
+    pair_tables_kernel<<<(unsigned)((LL + 255) / 256), 256, 0, st>>>(L, sub->d_D, sub->d_kappa, sub->d_dead,
+                                                                      d->dt_ms, q->d_T, d_warn);
+    if (N > 0)
+        step_tables_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, S, d->dt_ms, d_G, d_rec, d->n_rec,
+                                                                         q->d_wG64, q->d_wG32, q->d_flags,
+                                                                         q->d_rec_of);
+    bvalue_kernel<<<1, 32, 0, st>>>(N, S, d->dt_ms, d_G, d->n_b, q->d_b, q->d_bs, q->d_q);
+    RMS_CUDA(cudaGetLastError());
+    int32_t w = 0;
+    RMS_CUDA(cudaMemcpyAsync(&w, d_warn, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RMS_CUDA(cudaFreeAsync(d_G, st));
+    RMS_CUDA(cudaFreeAsync(d_rec, st));
+    RMS_CUDA(cudaFreeAsync(d_warn, st));
+    RMS_CUDA(cudaStreamSynchronize(st));
+    *warn = w != 0;
+    return RMS_OK;
+}
+
+extern "C" rms_status rms_set_sequence(rms_substrate *sub, const rms_sequence_desc *d, rms_sequence **out)
+{
+    if (!sub || !d || !out) return fail(RMS_E_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (!(d->dt_ms > 0.0) || !std::isfinite(d->dt_ms)) return fail(RMS_E_INVALID_ARG, "dt must be > 0");
+    if (d->n_steps < 0 || d->n_steps > 2000000000ll) return fail(RMS_E_INVALID_ARG, "n_steps out of range");
+    if (d->n_shapes < 1 || d->n_shapes > kMaxShapes) return fail(RMS_E_INVALID_ARG, "n_shapes must be 1..8");
+    if ((d->n_steps > 0 && !d->G) || d->n_dirs < 1 || !d->dirs || d->n_b < 1 || !d->b || d->n_rec < 0 ||
+        (d->n_rec > 0 && !d->rec_steps))
+        return fail(RMS_E_INVALID_ARG, "missing waveform, directions, b-values or recording steps");
+    rms_sequence *q = new (std::nothrow) rms_sequence();
+    if (!q) return fail(RMS_E_OOM, "host allocation");
+    bool warn = false;
+    rms_status r = set_sequence_impl(sub, d, q, &warn);
+    if (r < 0) {
+        free_sequence(q, 0);
+        cudaStreamSynchronize(0);
+        delete q;
+        return r;
+    }
+    sub->refs.fetch_add(1);
+    *out = q;
+    if (warn) {
+        g_last_error = "some permeation probability of Eq. 3 exceeded 1 and was clamped";
+        return RMS_W_PROB_RANGE;
+    }
+    return RMS_OK;
+}
+
+extern "C" rms_status rms_sequence_bvalues(const rms_sequence *q, double *bs)
+{
+    if (!q || !bs) return fail(RMS_E_INVALID_ARG, "null argument");
+    RMS_CUDA(cudaMemcpy(bs, q->d_bs, sizeof(double) * q->S, cudaMemcpyDeviceToHost));
+    return RMS_OK;
+}
+
+extern "C" rms_status rms_destroy_sequence(rms_sequence *q)
+{
+    if (!q) return RMS_OK;
+    if (q->refs.load() > 0) return fail(RMS_E_BUSY, "sequence still used by a run");
+    cudaDeviceSynchronize();
+    free_sequence(q, 0);
+    cudaStreamSynchronize(0);
+    q->sub->refs.fetch_sub(1);
+    delete q;
+    return RMS_OK;
+}
+
+// ------------------------------------------------------------------ run
+
+template <typename Real>
+static size_t layout_state(WalkerState<Real> &st, char *base, int64_t W, int S, bool hash, bool f32)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *p = base ? base + off : nullptr;
+        off += (bytes + 255) & ~size_t(255);
+        return p;
+    };
+    for (int a = 0; a < 3; ++a) st.o[a] = (Real *)take(sizeof(Real) * W);
+    for (int a = 0; a < 3; ++a) st.o0[a] = (Real *)take(sizeof(Real) * W);
+    for (int a = 0; a < 3; ++a) st.i0[a] = (int32_t *)take(sizeof(int32_t) * W);
+    for (int a = 0; a < 3; ++a) st.di[a] = (int32_t *)take(sizeof(int32_t) * W);
+    st.c = (int32_t *)take(sizeof(int32_t) * W);
+    st.A = (Real *)take(sizeof(Real) * W);
+    st.A_c = f32 ? (Real *)take(sizeof(Real) * W) : nullptr;
+    st.phase = (Real *)take(sizeof(Real) * W * S * 3);
+    st.phase_c = f32 ? (Real *)take(sizeof(Real) * W * S * 3) : nullptr;
+    st.hash = hash ? (uint64_t *)take(sizeof(uint64_t) * W) : nullptr;
+    return off;
+}
+
+template <typename Real>
+static rms_status enqueue_run(rms_run_handle *r, const WalkerState<Real> &st, const Tables<Real> &t, int32_t spl)
+{
+    rms_sequence *q = r->seq;
+    rms_substrate *sub = q->sub;
+    cudaStream_t s = r->stream;
+    const bool hash = (r->flags & RMS_TRAJ_HASH) != 0;
+    Geometry g{sub->d_labels, sub->nx, sub->ny, sub->nz, sub->periodic[0], sub->periodic[1], sub->periodic[2],
+               sub->voxel_um};
+    RunCtl ctl{};
+    ctl.seed = r->seed;
+    ctl.w_begin = r->w_begin;
+    ctl.n_walkers = r->W;
+    ctl.n_steps = q->n_steps;
+    ctl.n_shapes = q->S;
+    ctl.n_rec = q->n_rec;
+    ctl.status = r->d_status;
+    ctl.cancel = r->d_cancel;
+    ctl.mom_partial = r->d_mom_partial;
+    ctl.n_blocks = r->n_blocks;
+    const unsigned ib = (unsigned)((r->W + 255) / 256);
+    init_kernel<Real><<<ib, 256, 0, s>>>(g, sub->d_ok, sub->n_ok, st, ctl, hash);
+    RMS_CUDA(cudaGetLastError());
+    RMS_CUDA(cudaEventRecord(r->ev_start, s));
+    const dim3 grid((unsigned)r->n_blocks);
+    for (int64_t k0 = 0; k0 < q->n_steps; k0 += spl) {
+        const int64_t k1 = std::min<int64_t>(q->n_steps, k0 + spl);
+        RMS_CUDA(launch_walk<Real>(q->S, hash, grid, s, g, t, st, ctl, k0, k1));
+    }
+    RMS_CUDA(cudaEventRecord(r->ev_end, s));
+    if (q->n_rec > 0) {
+        moments_reduce_kernel<<<(q->n_rec * kMoments + 127) / 128, 128, 0, s>>>(r->d_mom_partial, q->n_rec,
+                                                                                r->n_blocks, r->d_mom);
+        RMS_CUDA(cudaGetLastError());
+    }
+    const dim3 rgrid((unsigned)((r->n_combo + 1 + kRoBlock - 1) / kRoBlock), (unsigned)r->n_chunks);
+    readout_kernel<Real><<<rgrid, kRoBlock, 0, s>>>(st.phase, st.phase_c, st.A, st.A_c, r->W, q->S, q->d_q,
+                                                    q->d_dirs, q->n_dirs, q->n_b, r->n_combo, r->d_ro_partial);
+    readout_reduce_kernel<<<(r->n_combo + 1 + 127) / 128, 128, 0, s>>>(r->d_ro_partial, r->n_chunks, r->n_combo,
+                                                                       r->d_S);
+    normalise_kernel<<<(r->n_combo + 127) / 128, 128, 0, s>>>(r->d_S, r->n_combo);
+    RMS_CUDA(cudaGetLastError());
+    return RMS_OK;
+}
+
+static void free_run(rms_run_handle *r)
+{
+    cudaStream_t s = r->stream;
+    void *p[] = {r->d_state, r->d_mom_partial, r->d_mom, r->d_ro_partial, r->d_S, r->d_status};
+    for (void *x : p)
+        if (x) cudaFreeAsync(x, s);
+    cudaStreamSynchronize(s);
+    if (r->h_cancel) cudaFreeHost(r->h_cancel);
+    if (r->ev_start) cudaEventDestroy(r->ev_start);
+    if (r->ev_end) cudaEventDestroy(r->ev_end);
+}
+
+static rms_status run_impl(rms_run_handle *r, int32_t spl)
+{
+    rms_sequence *q = r->seq;
+    cudaStream_t s = r->stream;
+    const bool hash = (r->flags & RMS_TRAJ_HASH) != 0;
+    const bool f32 = r->precision == RMS_FP32;
+    r->n_blocks = (int32_t)((r->W + walk_block_size() - 1) / walk_block_size());
+    r->n_combo = q->S * q->n_dirs * q->n_b;
+    r->n_chunks = (int32_t)((r->W + kRoChunk - 1) / kRoChunk);
+    const size_t bytes = f32 ? layout_state<float>(r->st32, nullptr, r->W, q->S, hash, true)
+                             : layout_state<double>(r->st64, nullptr, r->W, q->S, hash, false);
+    RMS_CUDA(cudaMallocAsync((void **)&r->d_state, bytes, s));
+    if (f32)
+        layout_state<float>(r->st32, r->d_state, r->W, q->S, hash, true);
+    else
+        layout_state<double>(r->st64, r->d_state, r->W, q->S, hash, false);
+    const size_t nmp = (size_t)std::max(q->n_rec, 1) * r->n_blocks * kMoments;
+    RMS_CUDA(cudaMallocAsync((void **)&r->d_mom_partial, sizeof(double) * nmp, s));
+    RMS_CUDA(cudaMallocAsync((void **)&r->d_mom, sizeof(double) * std::max(q->n_rec, 1) * kMoments, s));
+    RMS_CUDA(cudaMallocAsync((void **)&r->d_ro_partial, sizeof(double) * 2 * (size_t)(r->n_combo + 1) * r->n_chunks, s));
+    RMS_CUDA(cudaMallocAsync((void **)&r->d_S, sizeof(double) * 2 * (r->n_combo + 1), s));
+    RMS_CUDA(cudaMallocAsync((void **)&r->d_status, sizeof(int32_t), s));
+    RMS_CUDA(cudaMemsetAsync(r->d_status, 0, sizeof(int32_t), s));
+    RMS_CUDA(cudaHostAlloc((void **)&r->h_cancel, sizeof(int32_t), cudaHostAllocMapped));
+    *r->h_cancel = 0;
+    RMS_CUDA(cudaHostGetDevicePointer((void **)&r->d_cancel, r->h_cancel, 0));
+    RMS_CUDA(cudaEventCreate(&r->ev_start));
+    RMS_CUDA(cudaEventCreate(&r->ev_end));
+    if (f32) {
+        Tables<float> t{q->d_s32, q->d_dtR32, q->d_T, q->sub->L, q->d_wG32, q->d_flags, q->d_rec_of, q->d_mode,
+                        q->any_relax};
+        return enqueue_run<float>(r, r->st32, t, spl);
+    }
+    Tables<double> t{q->d_s64, q->d_dtR64, q->d_T, q->sub->L, q->d_wG64, q->d_flags, q->d_rec_of, q->d_mode,
+                     q->any_relax};
+    return enqueue_run<double>(r, r->st64, t, spl);
+}
+
+extern "C" rms_status rms_run(rms_sequence *q, const rms_run_desc *d, rms_run_handle **out)
+{
+    if (!q || !d || !out) return fail(RMS_E_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (d->n_walkers < 1 || d->n_walkers > (1ll << 31) - 1 || d->walker_begin < 0)
+        return fail(RMS_E_INVALID_ARG, "n_walkers must be in [1, 2^31) and walker_begin >= 0");
+    if (d->precision != RMS_FP64 && d->precision != RMS_FP32)
+        return fail(RMS_E_INVALID_ARG, "precision must be RMS_FP64 or RMS_FP32");
+    if (d->flags & ~RMS_TRAJ_HASH) return fail(RMS_E_INVALID_ARG, "unknown flag");
+    if (d->steps_per_launch < 0) return fail(RMS_E_INVALID_ARG, "steps_per_launch must be >= 0");
+    rms_run_handle *r = new (std::nothrow) rms_run_handle();
+    if (!r) return fail(RMS_E_OOM, "host allocation");
+    r->seq = q;
+    r->W = d->n_walkers;
+    r->w_begin = d->walker_begin;
+    r->seed = d->seed;
+    r->precision = d->precision;
+    r->flags = d->flags;
+    r->stream = (cudaStream_t)d->stream;
+    int32_t spl = d->steps_per_launch;
+    if (spl == 0) {
+        const int64_t target = 2000000000ll / std::max<int64_t>(r->W, 1);
+        spl = (int32_t)std::max<int64_t>(64, std::min<int64_t>(target, std::max<int64_t>(q->n_steps, 1)));
+    }
+    rms_status st = run_impl(r, spl);
+    if (st < 0) {
+        free_run(r);
+        delete r;
+        return st;
+    }
+    q->refs.fetch_add(1);
+    *out = r;
+    return RMS_OK;
+}
+
+extern "C" rms_status rms_run_query(rms_run_handle *r)
+{
+    if (!r) return fail(RMS_E_INVALID_ARG, "null run");
+    cudaError_t e = cudaStreamQuery(r->stream);
+    if (e == cudaErrorNotReady) return RMS_E_NOT_READY;
+    RMS_CUDA(e);
+    return RMS_OK;
+}
+
+extern "C" rms_status rms_cancel(rms_run_handle *r)
+{
+    if (!r) return fail(RMS_E_INVALID_ARG, "null run");
+    *(volatile int32_t *)r->h_cancel = 1;
+    return RMS_OK;
+}
+
+static rms_status finish(rms_run_handle *r)
+{
+    RMS_CUDA(cudaStreamSynchronize(r->stream));
+    if (*(volatile int32_t *)r->h_cancel) return fail(RMS_E_CANCELLED, "run was cancelled");
+    int32_t status = 0;
+    RMS_CUDA(cudaMemcpy(&status, r->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (status & kErrFourthEvent)
+        return fail(RMS_E_DEVICE, "a step met a fourth face (some step length >= voxel size)");
+    if (status & kErrDirection) return fail(RMS_E_DEVICE, "direction sampler exhausted its draws");
+    if (status) return fail(RMS_E_DEVICE, "device status " + std::to_string(status));
+    return RMS_OK;
+}
+
+extern "C" rms_status rms_read_signal(rms_run_handle *r, double *S_re, double *S_im, double *moments, double *alpha_sum)
+{
+    if (!r) return fail(RMS_E_INVALID_ARG, "null run");
+    RMS_TRY(finish(r));
+    std::vector<double> S((size_t)2 * (r->n_combo + 1));
+    RMS_CUDA(cudaMemcpy(S.data(), r->d_S, sizeof(double) * S.size(), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < r->n_combo; ++k) {
+        if (S_re) S_re[k] = S[2 * k];
+        if (S_im) S_im[k] = S[2 * k + 1];
+    }
+    if (alpha_sum) *alpha_sum = S[2 * r->n_combo];
+    if (moments && r->seq->n_rec > 0)
+        RMS_CUDA(cudaMemcpy(moments, r->d_mom, sizeof(double) * r->seq->n_rec * kMoments, cudaMemcpyDeviceToHost));
+    return RMS_OK;
+}
+
+extern "C" rms_status rms_read_walkers(rms_run_handle *r, int32_t *i, double *o, int32_t *i0, double *o0, int32_t *c,
+                                       double *A, double *phase, uint64_t *hash)
+{
+    if (!r) return fail(RMS_E_INVALID_ARG, "null run");
+    RMS_TRY(finish(r));
+    const int64_t W = r->W;
+    const int S = r->seq->S;
+    cudaStream_t s = r->stream;
+    char *buf = nullptr;
+    const size_t bi = sizeof(int32_t) * 3 * W, bo = sizeof(double) * 3 * W, bc = sizeof(int32_t) * W,
+                 bA = sizeof(double) * W, bp = sizeof(double) * 3 * S * W, bh = sizeof(uint64_t) * W;
+    // every sub-buffer starts on a 256-byte boundary
+    const size_t sizes[8] = {bi, bi, bo, bo, bc, bA, bp, bh};
+    size_t offs[8], total = 0;
+    for (int k = 0; k < 8; ++k) {
+        offs[k] = total;
+        total += (sizes[k] + 255) & ~size_t(255);
+    }
+    RMS_CUDA(cudaMallocAsync((void **)&buf, total, s));
+    int32_t *di = (int32_t *)(buf + offs[0]), *di0 = (int32_t *)(buf + offs[1]);
+    double *dO = (double *)(buf + offs[2]), *dO0 = (double *)(buf + offs[3]);
+    int32_t *dc = (int32_t *)(buf + offs[4]);
+    double *dA = (double *)(buf + offs[5]);
+    double *dp = (double *)(buf + offs[6]);
+    uint64_t *dh = (uint64_t *)(buf + offs[7]);
+    const unsigned nb = (unsigned)((W + 255) / 256);
+    const bool hsh = (r->flags & RMS_TRAJ_HASH) != 0;
+    if (r->precision == RMS_FP32)
+        export_kernel<float><<<nb, 256, 0, s>>>(r->st32, W, S, hsh, di, dO, di0, dO0, dc, dA, dp, dh);
+    else
+        export_kernel<double><<<nb, 256, 0, s>>>(r->st64, W, S, hsh, di, dO, di0, dO0, dc, dA, dp, dh);
+    RMS_CUDA(cudaGetLastError());
+    struct {
+        void *h;
+        const void *d;
+        size_t n;
+    } cp[] = {{i, di, bi}, {i0, di0, bi}, {o, dO, bo}, {o0, dO0, bo}, {c, dc, bc}, {A, dA, bA}, {phase, dp, bp},
+              {hash, dh, bh}};
+    for (auto &x : cp)
+        if (x.h) RMS_CUDA(cudaMemcpyAsync(x.h, x.d, x.n, cudaMemcpyDeviceToHost, s));
+    RMS_CUDA(cudaFreeAsync(buf, s));
+    RMS_CUDA(cudaStreamSynchronize(s));
+    return RMS_OK;
+}
+
+extern "C" rms_status rms_run_step_time_ms(rms_run_handle *r, float *ms)
+{
+    if (!r || !ms) return fail(RMS_E_INVALID_ARG, "null argument");
+    RMS_CUDA(cudaEventSynchronize(r->ev_end));
+    RMS_CUDA(cudaEventElapsedTime(ms, r->ev_start, r->ev_end));
+    return RMS_OK;
+}
+
+extern "C" rms_status rms_destroy_run(rms_run_handle *r)
+{
+    if (!r) return RMS_OK;
+    cudaStreamSynchronize(r->stream);
+    free_run(r);
+    r->seq->refs.fetch_sub(1);
+    delete r;
+    return RMS_OK;
+}

@@ -1,0 +1,109 @@
+// rms_device.cuh -- device-side building blocks shared by the library's own
+// translation units: the counter-based generator, the checksum mixer and the
+// parameter blocks handed to the kernels.
+#pragma once
+
+#include <cstdint>
+
+namespace rms {
+
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds; in each,
+// the even words are multiplied by the two round multipliers, the high
+// halves are XOR-ed with the odd words and the key, and the key advances by
+// the two Weyl increments between rounds.
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Counter layout: key (seed_lo, seed_hi); counter (walker_lo, walker_hi,
+// step, tag << 16 | call).
+enum : uint32_t { kTagInit = 1u, kTagDir = 2u, kTagPerm = 3u };
+
+__device__ __forceinline__ U4 draw(uint64_t seed, uint64_t w, uint32_t step, uint32_t tag,
+                                   uint32_t call)
+{
+    return philox4x32_10(U4{(uint32_t)w, (uint32_t)(w >> 32), step, (tag << 16) | call},
+                         (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// (x + 1/2) 2^-32: uniform in (0,1), exact in FP64.
+__device__ __forceinline__ double u01(uint32_t x) { return ((double)x + 0.5) * 0x1p-32; }
+
+// SplitMix64 finaliser (Steele, Lea & Flood 2014), the trajectory checksum.
+__device__ __forceinline__ uint64_t mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+constexpr int kMoments = 22;  // alpha, 6 second-order, 15 fourth-order terms
+constexpr int kMaxShapes = 8;
+
+// Device error bits (status word).
+enum : int { kErrFourthEvent = 1, kErrDirection = 2, kErrTimeout = 4 };
+
+// Walker state, structure of arrays, one entry per walker.
+template <typename Real>
+struct WalkerState {
+    Real *o[3];        // offset inside the voxel, [0,1]
+    Real *o0[3];       // initial offset
+    int32_t *i0[3];    // initial voxel (wrapped coordinates)
+    int32_t *di[3];    // unwrapped voxel displacement i - i0
+    int32_t *c;        // current label
+    Real *A;           // relaxation exponent (FP32 form: Kahan sum with A_c)
+    Real *A_c;         // Kahan compensation (FP32 form only)
+    Real *phase;       // [shape][axis][W]
+    Real *phase_c;     // Kahan compensation (FP32 form only), same layout
+    uint64_t *hash;
+};
+
+struct Geometry {
+    const uint16_t *labels;
+    int32_t nx, ny, nz;
+    int32_t per_x, per_y, per_z;
+    double voxel_um;
+};
+
+template <typename Real>
+struct Tables {
+    const Real *s;          // step length per label, voxel units
+    const Real *dtR;        // [mode][label]: dt / T (0 = none)
+    const uint32_t *T;      // [from][to] Bernoulli thresholds
+    int32_t n_labels;
+    const Real *wG;         // [shape][step]: dt * G
+    const uint8_t *flags;   // [step]: bit0 any G != 0, bit1 recording step
+    const int32_t *rec_of;  // [step]: recording index or -1
+    const uint8_t *mode;    // [step] relaxation mode (or nullptr = 0)
+    int32_t any_relax;
+};
+
+struct RunCtl {
+    uint64_t seed;
+    int64_t w_begin;
+    int64_t n_walkers;
+    int64_t n_steps;
+    int32_t n_shapes;
+    int32_t n_rec;
+    int32_t *status;                // device error bits
+    const volatile int32_t *cancel; // host-mapped cancel flag (nullptr = none)
+    double *mom_partial;            // [rec][block][22]
+    int32_t n_blocks;
+};
+
+}  // namespace rms

@@ -1,0 +1,24 @@
+// rms_internal.h -- declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rms_device.cuh"
+
+namespace rms {
+
+template <typename Real>
+cudaError_t launch_walk(int n_shapes, bool hash, dim3 grid, cudaStream_t stream, const Geometry &g,
+                        const Tables<Real> &t, const WalkerState<Real> &st, const RunCtl &ctl,
+                        int64_t k_begin, int64_t k_end);
+
+extern template cudaError_t launch_walk<double>(int, bool, dim3, cudaStream_t, const Geometry &,
+                                                const Tables<double> &, const WalkerState<double> &,
+                                                const RunCtl &, int64_t, int64_t);
+extern template cudaError_t launch_walk<float>(int, bool, dim3, cudaStream_t, const Geometry &,
+                                               const Tables<float> &, const WalkerState<float> &,
+                                               const RunCtl &, int64_t, int64_t);
+
+int walk_block_size();
+
+}  // namespace rms

@@ -1,0 +1,419 @@
+// walk_kernel.cuh -- the random-walker time step (Sec. 2.2 items 2-5 of
+// Lee, Fieremans & Novikov, arXiv 2012.06478), templated on the arithmetic
+// type.  Included by walk_fp64.cu (built without FMA contraction: the plain
+// form reproduces the CPU FP64 reference bit for bit) and walk_fp32.cu (the
+// precision form: voxel index + FP32 offset, FP32 Kahan-compensated phase).
+//
+// One thread owns one walker for a slice of steps; its whole state stays in
+// registers for the slice and goes back to global memory (structure of
+// arrays, coalesced) at the end.  Per step and walker the only memory
+// traffic is the dependent 2-byte label gather across each face met
+// (Sec. 2.1.1: the label volume is the lookup table), the threshold of the
+// label pair at a membrane, and warp-uniform broadcasts of the waveform.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include "rms_device.cuh"
+
+namespace rms {
+
+constexpr int kWalkBlock = 128;
+constexpr int kWalkWarps = kWalkBlock / 32;
+
+template <typename Real>
+__device__ __forceinline__ Real clamp01(Real x)
+{
+    if (x < Real(0)) return Real(0);
+    if (x > Real(1)) return Real(1);
+    return x;
+}
+
+// Sec. 2.2 item 2, the direction: Marsaglia (1972) from two 32-bit words,
+// v = 2u - 1, accept s = v1^2 + v2^2 < 1, n = (2 v1 r, 2 v2 r, 1 - 2 s),
+// r = sqrt(1 - s).
+__device__ __forceinline__ bool marsaglia(uint32_t a, uint32_t b, double n[3])
+{
+    const double v1 = 2.0 * u01(a) - 1.0;
+    const double v2 = 2.0 * u01(b) - 1.0;
+    const double s = v1 * v1 + v2 * v2;
+    if (!(s < 1.0)) return false;
+    const double r = sqrt(1.0 - s);
+    n[0] = (2.0 * v1) * r;
+    n[1] = (2.0 * v2) * r;
+    n[2] = 1.0 - 2.0 * s;
+    return true;
+}
+
+// FP32 form of the same sampler: v from the word's signed value.
+__device__ __forceinline__ bool marsaglia(uint32_t a, uint32_t b, float n[3])
+{
+    const float v1 = __int2float_rn((int32_t)(a ^ 0x80000000u)) * 0x1p-31f;
+    const float v2 = __int2float_rn((int32_t)(b ^ 0x80000000u)) * 0x1p-31f;
+    const float s = v1 * v1 + v2 * v2;
+    if (!(s < 1.0f)) return false;
+    const float r = sqrtf(1.0f - s);
+    n[0] = (2.0f * v1) * r;
+    n[1] = (2.0f * v2) * r;
+    n[2] = 1.0f - 2.0f * s;
+    return true;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename Real>
+__device__ __forceinline__ void kahan_add(Real &sum, Real &comp, Real x)
+{
+    const Real y = x - comp;
+    const Real t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+// The 22 moment terms at a recording step (Sec. 2.3, narrow-pulse D and K):
+// alpha, alpha dx_i dx_j (i <= j), alpha dx_i dx_j dx_k dx_l (i<=j<=k<=l).
+__device__ __forceinline__ void moment_terms(double al, const double dx[3], double m[kMoments])
+{
+    int p = 0;
+    m[p++] = al;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a; b < 3; ++b) m[p++] = al * dx[a] * dx[b];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a; b < 3; ++b)
+#pragma unroll
+            for (int c = b; c < 3; ++c)
+#pragma unroll
+                for (int d = c; d < 3; ++d) m[p++] = al * dx[a] * dx[b] * dx[c] * dx[d];
+}
+
+// Steps (k_begin, k_end] for every walker of the run.
+template <typename Real, int NS, bool HASH>
+__global__ void __launch_bounds__(kWalkBlock)
+walk_kernel(Geometry g, Tables<Real> t, WalkerState<Real> st, RunCtl ctl, int64_t k_begin,
+            int64_t k_end)
+{
+    constexpr bool kF64 = std::is_same<Real, double>::value;
+    __shared__ int32_t s_cancel;
+    __shared__ double s_red[kWalkWarps][kMoments];
+    if (threadIdx.x == 0) s_cancel = ctl.cancel ? *ctl.cancel : 0;
+    __syncthreads();
+    if (s_cancel) return;
+
+    const int64_t li = (int64_t)blockIdx.x * kWalkBlock + threadIdx.x;
+    const bool active = li < ctl.n_walkers;
+    const uint64_t w = (uint64_t)(ctl.w_begin + li);
+    const int32_t N[3] = {g.nx, g.ny, g.nz};
+    const int32_t stride[3] = {1, g.nx, g.nx * g.ny};
+    const int32_t per[3] = {g.per_x, g.per_y, g.per_z};
+    const int32_t L = t.n_labels;
+
+    Real o[3], o0[3];
+    int32_t di[3], wc[3];
+    int32_t v = 0, c = 0;
+    Real A = Real(0), Ac = Real(0);
+    Real ph[NS][3], phc[NS][3];
+    uint64_t h = 0;
+    if (active) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o[a] = st.o[a][li];
+            o0[a] = st.o0[a][li];
+            di[a] = st.di[a][li];
+            int32_t q = (st.i0[a][li] + di[a]) % N[a];
+            wc[a] = q < 0 ? q + N[a] : q;
+        }
+        v = wc[0] + stride[1] * wc[1] + stride[2] * wc[2];
+        c = st.c[li];
+        A = st.A[li];
+        if (!kF64) Ac = st.A_c[li];
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                ph[s][a] = s < ctl.n_shapes ? st.phase[((int64_t)s * 3 + a) * ctl.n_walkers + li] : Real(0);
+                phc[s][a] = (!kF64 && s < ctl.n_shapes)
+                                ? st.phase_c[((int64_t)s * 3 + a) * ctl.n_walkers + li]
+                                : Real(0);
+            }
+        if (HASH) h = st.hash[li];
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o[a] = o0[a] = Real(0);
+            di[a] = wc[a] = 0;
+        }
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) ph[s][a] = phc[s][a] = Real(0);
+    }
+
+    for (int64_t k = k_begin + 1; k <= k_end; ++k) {
+        const uint8_t fl = __ldg(t.flags + (k - 1));
+        if (active) {
+            // ---- direction (DIR stream)
+            Real n[3];
+            bool ok = false;
+            for (uint32_t call = 0; call < 64u && !ok; ++call) {
+                const U4 x = draw(ctl.seed, w, (uint32_t)k, kTagDir, call);
+                ok = marsaglia(x.x, x.y, n) || marsaglia(x.z, x.w, n);
+            }
+            if (!ok) {
+                atomicOr(ctl.status, kErrDirection);
+                n[0] = Real(0);
+                n[1] = Real(0);
+                n[2] = Real(1);
+            }
+            // ---- face walk (Sec. 2.2 items 3-4)
+            const int mode = t.mode ? (int)__ldg(t.mode + (k - 1)) : 0;
+            Real sc = __ldg(t.s + c);
+            Real rate = t.any_relax ? __ldg(t.dtR + mode * L + c) : Real(0);
+            Real d[3] = {n[0] * sc, n[1] * sc, n[2] * sc};
+            Real f = Real(1);
+            bool have_perm = false;
+            U4 perm = U4{0u, 0u, 0u, 0u};
+            for (int ev = 0;; ++ev) {
+                int best = -1;
+                Real tbest = Real(0);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    Real dist, ad;
+                    bool cand = true;
+                    if (d[a] > Real(0)) {
+                        dist = Real(1) - o[a];
+                        ad = d[a];
+                    } else if (d[a] < Real(0)) {
+                        dist = o[a];
+                        ad = -d[a];
+                    } else {
+                        cand = false;
+                        dist = ad = Real(1);
+                    }
+                    if (cand && dist < f * ad) {
+                        const Real tt = dist / ad;
+                        if (best < 0 || tt < tbest) {
+                            best = a;
+                            tbest = tt;
+                        }
+                    }
+                }
+                if (best < 0 || ev == 3) {
+                    if (best >= 0) atomicOr(ctl.status, kErrFourthEvent);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) o[a] = clamp01(o[a] + f * d[a]);
+                    if (t.any_relax) {
+                        if (kF64)
+                            A = A + f * rate;
+                        else
+                            kahan_add(A, Ac, f * rate);
+                    }
+                    break;
+                }
+                const Real tt = tbest < f ? tbest : f;
+                bool up = false;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (a == best) {
+                        up = d[a] > Real(0);
+                        o[a] = up ? Real(1) : Real(0);
+                    } else {
+                        o[a] = clamp01(o[a] + tt * d[a]);
+                    }
+                }
+                if (t.any_relax) {
+                    if (kF64)
+                        A = A + tt * rate;
+                    else
+                        kahan_add(A, Ac, tt * rate);
+                }
+                f = f - tt;
+                // the voxel across the face
+                int32_t coord = 0, Nb = 1, sb = 1, pb = 1;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    if (a == best) {
+                        coord = wc[a];
+                        Nb = N[a];
+                        sb = stride[a];
+                        pb = per[a];
+                    }
+                int32_t nc, nv;
+                bool wall = false;
+                if (up) {
+                    nc = coord + 1;
+                    nv = v + sb;
+                    if (nc == Nb) {
+                        wall = !pb;
+                        nc = 0;
+                        nv = v - (Nb - 1) * sb;
+                    }
+                } else {
+                    nc = coord - 1;
+                    nv = v - sb;
+                    if (coord == 0) {
+                        wall = !pb;
+                        nc = Nb - 1;
+                        nv = v + (Nb - 1) * sb;
+                    }
+                }
+                int32_t c2 = wall ? -1 : (int32_t)__ldg(g.labels + nv);
+                bool cross;
+                if (c2 == c) {
+                    cross = true;
+                } else if (c2 < 0) {
+                    cross = false;
+                } else {
+                    const uint32_t T = __ldg(t.T + (int64_t)c * L + c2);
+                    if (T == 0u) {
+                        cross = false;
+                    } else {
+                        if (!have_perm) {
+                            perm = draw(ctl.seed, w, (uint32_t)k, kTagPerm, 0u);
+                            have_perm = true;
+                        }
+                        const uint32_t word = ev == 0 ? perm.x : (ev == 1 ? perm.y : perm.z);
+                        cross = word < T;
+                    }
+                }
+                if (cross) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        if (a == best) {
+                            wc[a] = nc;
+                            di[a] += up ? 1 : -1;
+                            o[a] = up ? Real(0) : Real(1);
+                        }
+                    v = nv;
+                    if (c2 != c) {
+                        c = c2;
+                        sc = __ldg(t.s + c);
+                        if (t.any_relax) rate = __ldg(t.dtR + mode * L + c);
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) d[a] = n[a] * sc;
+                    }
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        if (a == best) {
+                            n[a] = -n[a];
+                            d[a] = -d[a];
+                        }
+                }
+            }
+            if (HASH) {
+                const uint64_t x = (((uint64_t)k & 0xFFFFu) << 48) ^ ((uint64_t)(uint32_t)c << 32) ^
+                                   (uint64_t)(uint32_t)v;
+                h = mix64(h ^ x);
+            }
+            // ---- phase (Eq. 7, right end point of each step)
+            if (fl & 1u) {
+                Real dx[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    dx[a] = (Real)g.voxel_um * ((Real)di[a] + (o[a] - o0[a]));
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    if (s < ctl.n_shapes) {
+                        const Real wg = __ldg(t.wG + (int64_t)s * ctl.n_steps + (k - 1));
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            if (kF64)
+                                ph[s][a] = ph[s][a] + wg * dx[a];
+                            else
+                                kahan_add(ph[s][a], phc[s][a], wg * dx[a]);
+                        }
+                    }
+                }
+            }
+        }
+        // ---- displacement moments at recording steps (block-uniform branch)
+        if (fl & 2u) {
+            double m[kMoments];
+            if (active) {
+                double dx[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    dx[a] = g.voxel_um * ((double)di[a] + ((double)o[a] - (double)o0[a]));
+                const double al = kF64 ? exp(-(double)A) : exp(-((double)A - (double)Ac));
+                moment_terms(al, dx, m);
+            } else {
+#pragma unroll
+                for (int q = 0; q < kMoments; ++q) m[q] = 0.0;
+            }
+            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+            for (int q = 0; q < kMoments; ++q) {
+                const double r = warp_sum(m[q]);
+                if (lane == 0) s_red[wid][q] = r;
+            }
+            __syncthreads();
+            if (threadIdx.x < kMoments) {
+                double acc = 0.0;
+#pragma unroll
+                for (int ww = 0; ww < kWalkWarps; ++ww) acc += s_red[ww][threadIdx.x];
+                const int32_t r = __ldg(t.rec_of + (k - 1));
+                ctl.mom_partial[((int64_t)r * ctl.n_blocks + blockIdx.x) * kMoments + threadIdx.x] = acc;
+            }
+            __syncthreads();
+        }
+    }
+
+    if (active) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            st.o[a][li] = o[a];
+            st.di[a][li] = di[a];
+        }
+        st.c[li] = c;
+        st.A[li] = A;
+        if (!kF64) st.A_c[li] = Ac;
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+            if (s < ctl.n_shapes)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    st.phase[((int64_t)s * 3 + a) * ctl.n_walkers + li] = ph[s][a];
+                    if (!kF64) st.phase_c[((int64_t)s * 3 + a) * ctl.n_walkers + li] = phc[s][a];
+                }
+        if (HASH) st.hash[li] = h;
+    }
+}
+
+// Host-side launcher, instantiated in walk_fp64.cu / walk_fp32.cu.
+template <typename Real>
+cudaError_t launch_walk(int n_shapes, bool hash, dim3 grid, cudaStream_t stream, const Geometry &g,
+                        const Tables<Real> &t, const WalkerState<Real> &st, const RunCtl &ctl,
+                        int64_t k_begin, int64_t k_end)
+{
+#define RMS_LAUNCH(NSV)                                                                          \
+    do {                                                                                         \
+        if (hash)                                                                                \
+            walk_kernel<Real, NSV, true><<<grid, kWalkBlock, 0, stream>>>(g, t, st, ctl, k_begin, \
+                                                                         k_end);                 \
+        else                                                                                     \
+            walk_kernel<Real, NSV, false><<<grid, kWalkBlock, 0, stream>>>(g, t, st, ctl,        \
+                                                                          k_begin, k_end);       \
+    } while (0)
+    if (n_shapes <= 1)
+        RMS_LAUNCH(1);
+    else if (n_shapes <= 2)
+        RMS_LAUNCH(2);
+    else if (n_shapes <= 4)
+        RMS_LAUNCH(4);
+    else
+        RMS_LAUNCH(8);
+#undef RMS_LAUNCH
+    return cudaGetLastError();
+}
+
+}  // namespace rms
