@@ -188,6 +188,39 @@ rms_status rms_destroy_run(rms_run_handle *run);
  * step launch of a finished run; synchronises. */
 rms_status rms_run_step_time_ms(rms_run_handle *run, float *ms);
 
+/* ------------------------------------------------------------------ */
+/* Signal read-out that allocates nothing.  The paper has no           */
+/* counterpart: this is a service for callers that may not allocate    */
+/* device memory at the point of the call -- for example a serving     */
+/* loop sharing the GPU with other streams (cudaMalloc and cudaFree    */
+/* can synchronise the whole device and stall them), or an application */
+/* whose device memory all belongs to its own fixed pool or arena.     */
+/* ------------------------------------------------------------------ */
+#define RMS_NOALLOC_SCRATCH_BYTES (8 * 1024 * 1024)
+
+/* The same read-out as rms_run's (Eq. 7: S = sum alpha e^{-i phi} / sum
+ * alpha, phi = q g.Phi_s, q = sqrt(b / b_s), alpha = exp(-A)) over walker data
+ * the caller holds.  Every pointer is a DEVICE pointer of the current device:
+ *   phase     : n_walkers*n_shapes*3 doubles, row-major (walker, shape, axis),
+ *               the layout rms_read_walkers returns
+ *   A         : n_walkers doubles, exponent of Eq. 5
+ *   b_s       : n_shapes doubles (rms_sequence_bvalues), dirs: n_dirs*3, b: n_b
+ *   S_re, S_im: outputs, n_shapes*n_dirs*n_b doubles, index (shape*n_dirs + dir)*n_b + b
+ *   alpha_sum : output, 1 double (may be NULL)
+ * The work is enqueued on `stream` (cudaStream_t) and the call returns
+ * without waiting.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine: its scratch is a fixed RMS_NOALLOC_SCRATCH_BYTES array inside the
+ * library, present on every GPU that loads the library until the process
+ * exits.  The first call on each device looks up that array's address (do it
+ * before any stream capture on that device).  All calls share the array:
+ * calls that may overlap on the GPU (other streams, other host threads) must
+ * be serialised by the caller.  Errors: RMS_E_INVALID_ARG (null pointer,
+ * n_walkers < 1, n_shapes outside 1..8, or 2*(n_shapes*n_dirs*n_b + 1) doubles
+ * not fitting the scratch), RMS_E_CUDA. */
+rms_status rms_readout_noalloc(const double *phase, const double *A, int64_t n_walkers, int32_t n_shapes,
+                               const double *b_s, int32_t n_dirs, const double *dirs, int32_t n_b,
+                               const double *b, double *S_re, double *S_im, double *alpha_sum, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

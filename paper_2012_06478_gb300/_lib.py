@@ -68,6 +68,8 @@ SIGNATURES = {
     "rms_read_walkers": ([C.c_void_p] + [C.c_void_p] * 8, C.c_int),
     "rms_destroy_run": ([C.c_void_p], C.c_int),
     "rms_run_step_time_ms": ([C.c_void_p, C.POINTER(C.c_float)], C.c_int),
+    "rms_readout_noalloc": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
+                             C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 }
 
 

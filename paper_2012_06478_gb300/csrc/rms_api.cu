@@ -38,6 +38,8 @@ static rms_status fail(rms_status st, const std::string &msg)
                         std::string(#call) + ": " + cudaGetErrorString(e_));                     \
     } while (0)
 
+void rms::set_last_error(const char *msg) { g_last_error = msg; }
+
 extern "C" int rms_version(void) { return 10000; }
 extern "C" const char *rms_last_error(void) { return g_last_error.c_str(); }
 

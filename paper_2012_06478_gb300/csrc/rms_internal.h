@@ -21,4 +21,7 @@ extern template cudaError_t launch_walk<float>(int, bool, dim3, cudaStream_t, co
 
 int walk_block_size();
 
+// Message returned by rms_last_error() on the calling thread.
+void set_last_error(const char *msg);
+
 }  // namespace rms
