@@ -95,6 +95,7 @@ def lib():
         _lib.rmso_thresholds.restype = C.c_int
         _lib.rmso_direction.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_void_p]
         _lib.rmso_direction.restype = C.c_int
+        _lib.rmso_direction_from_words.argtypes = [C.c_uint32, C.c_uint32, C.c_void_p]
     return _lib
 
 
@@ -133,6 +134,12 @@ def direction(seed: int, w: int, k: int) -> np.ndarray:
     n = np.zeros(3)
     if lib().rmso_direction(seed, w, k, n.ctypes.data):
         raise RuntimeError("direction sampler ran out of draws")
+    return n
+
+
+def direction_from_words(x0: int, x1: int) -> np.ndarray:
+    n = np.zeros(3)
+    lib().rmso_direction_from_words(x0, x1, n.ctypes.data)
     return n
 
 
@@ -240,7 +247,7 @@ def thresholds(wl):
     return T, s
 
 
-def walk_once(wl, i, o, c, n, perm=(0, 0, 0, 0), A=0.0, mode=0):
+def walk_once(wl, i, o, c, n, perm=(0, 0, 0), A=0.0, mode=0):
     """One face walk of a single walker with a given direction n and given
     PERM words (no random draws).  Returns (i, o, c, A, n, counts, err)."""
     keep = _Keep()
@@ -250,7 +257,8 @@ def walk_once(wl, i, o, c, n, perm=(0, 0, 0, 0), A=0.0, mode=0):
     cc = np.array([c], np.int32)
     AA = np.array([A], np.float64)
     nn = np.array(n, np.float64)
-    pp = np.array(perm, np.uint32)
+    pp = np.zeros(4, np.uint32)
+    pp[:len(perm)] = perm
     counts = np.zeros(3, np.int64)
     err = lib().rmso_walk_once(C.byref(cfg), ii.ctypes.data, oo.ctypes.data, cc.ctypes.data,
                                AA.ctypes.data, nn.ctypes.data, pp.ctypes.data, mode, counts.ctypes.data)

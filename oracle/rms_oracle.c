@@ -49,7 +49,6 @@
 
 /* error bits reported through rmso_run's return value */
 #define RMSO_ERR_FOURTH_EVENT 1
-#define RMSO_ERR_DIRECTION 2
 #define RMSO_ERR_BAD_ARG 4
 #define RMSO_ERR_OOM 8
 
@@ -309,28 +308,68 @@ static void init_walker(const ctx *X, uint64_t w, walker *s)
 }
 
 /* Sec. 2.2 item 2, direction sampler (the paper does not name one):
- * Marsaglia (1972).  Each DIR call gives two attempts, word pairs (0,1)
- * and (2,3): v = 2u - 1, s = v1^2 + v2^2, accept s < 1, then
- * n = (2 v1 sqrt(1-s), 2 v2 sqrt(1-s), 1 - 2 s), a uniform unit vector. */
-static int direction(uint64_t seed, uint64_t w, uint32_t k, double n[3])
+ * Archimedes' hat-box theorem -- z = 1 - 2u is uniform on [-1,1] for a
+ * uniform point of the sphere -- with the azimuth phi = 2 pi (x1 + 1/2) 2^-32
+ * from the second word.  sin and cos of the azimuth come from Taylor
+ * polynomials on [0, pi/4] (degree 17 / 16, truncation < 1e-18), after an
+ * octant reduction done in integers, so only +, *, sqrt are used and the
+ * result is the same bits on every IEEE machine.  One DIR call (k, call 0)
+ * per step: words 0 and 1 give the direction, words 2 and 3 are the PERM
+ * words of the step's first two membrane events. */
+static const double kPi4 = 0.78539816339744830962; /* pi/4 */
+
+static void direction_from(uint32_t x0, uint32_t x1, double n[3])
 {
-    for (uint32_t call = 0; call < 64; call++) {
-        uint32_t x[4];
-        draw(seed, w, k, TAG_DIR, call, x);
-        for (int pair = 0; pair < 2; pair++) {
-            double v1 = 2.0 * u01(x[2 * pair]) - 1.0;
-            double v2 = 2.0 * u01(x[2 * pair + 1]) - 1.0;
-            double s = v1 * v1 + v2 * v2;
-            if (s < 1.0) {
-                double r = sqrt(1.0 - s);
-                n[0] = (2.0 * v1) * r;
-                n[1] = (2.0 * v2) * r;
-                n[2] = 1.0 - 2.0 * s;
-                return 0;
-            }
-        }
+    const double z = 1.0 - 2.0 * u01(x0);
+    const double r = sqrt((1.0 - z) * (1.0 + z));
+    const uint32_t oct = x1 >> 29;
+    uint32_t m = x1 & 0x1FFFFFFFu;
+    if (oct & 1u) m = 0x1FFFFFFFu - m; /* odd octant: angle measured back from the octant's end */
+    const double th = (((double)m + 0.5) * 0x1p-29) * kPi4;
+    const double t = th * th;
+    double ps = 1.0 / 355687428096000.0;       /*  1/17! */
+    ps = -1.0 / 1307674368000.0 + t * ps;       /* -1/15! */
+    ps = 1.0 / 6227020800.0 + t * ps;           /*  1/13! */
+    ps = -1.0 / 39916800.0 + t * ps;            /* -1/11! */
+    ps = 1.0 / 362880.0 + t * ps;               /*  1/9!  */
+    ps = -1.0 / 5040.0 + t * ps;                /* -1/7!  */
+    ps = 1.0 / 120.0 + t * ps;                  /*  1/5!  */
+    ps = -1.0 / 6.0 + t * ps;                   /* -1/3!  */
+    const double sn = th + (th * t) * ps;
+    double pc = 1.0 / 20922789888000.0;         /*  1/16! */
+    pc = -1.0 / 87178291200.0 + t * pc;         /* -1/14! */
+    pc = 1.0 / 479001600.0 + t * pc;            /*  1/12! */
+    pc = -1.0 / 3628800.0 + t * pc;             /* -1/10! */
+    pc = 1.0 / 40320.0 + t * pc;                /*  1/8!  */
+    pc = -1.0 / 720.0 + t * pc;                 /* -1/6!  */
+    pc = 1.0 / 24.0 + t * pc;                   /*  1/4!  */
+    pc = -1.0 / 2.0 + t * pc;                   /* -1/2!  */
+    const double cs = 1.0 + t * pc;
+    double cx, sy; /* cos and sin of oct pi/4 + th (even) or (oct+1) pi/4 - th (odd) */
+    switch (oct) {
+    case 0: cx = cs; sy = sn; break;
+    case 1: cx = sn; sy = cs; break;
+    case 2: cx = -sn; sy = cs; break;
+    case 3: cx = -cs; sy = sn; break;
+    case 4: cx = -cs; sy = -sn; break;
+    case 5: cx = -sn; sy = -cs; break;
+    case 6: cx = sn; sy = -cs; break;
+    default: cx = cs; sy = -sn; break;
     }
-    return RMSO_ERR_DIRECTION;
+    n[0] = r * cx;
+    n[1] = r * sy;
+    n[2] = z;
+}
+
+/* The step's DIR call: direction from words 0, 1; PERM words 0, 1 from
+ * words 2, 3. */
+static void direction(uint64_t seed, uint64_t w, uint32_t k, double n[3], uint32_t perm01[2])
+{
+    uint32_t x[4];
+    draw(seed, w, k, TAG_DIR, 0u, x);
+    direction_from(x[0], x[1], n);
+    perm01[0] = x[2];
+    perm01[1] = x[3];
 }
 
 static double clamp01(double x)
@@ -357,13 +396,13 @@ static double clamp01(double x)
  *     word[e] < T[c][c'] (Eq. 3)    -> cross into c'; the remaining fraction f
  *                                      is kept and the step length becomes s_c'
  *     otherwise                     -> reflect: n_a = -n_a (elastic collision)
- *   where word[e] is word e of PERM call 0 and e the index of this event in
- *   the step.  With s_c < 1 for every label each axis meets at most one face
+ *   where e is the index of this event in the step and word[0], word[1]
+ *   are words 2, 3 of the step's DIR call, word[2] word 0 of its PERM call.  With s_c < 1 for every label each axis meets at most one face
  *   per step (the corner reflector), so a fourth event is an error.
  * Every coordinate is clamped to [0,1] after each move.  The relaxation
  * exponent accumulates (segment fraction) x (dt / T of the segment's label). */
 static int walk_step(const ctx *X, uint64_t w, uint32_t k, walker *s, double n[3],
-                     const uint32_t *perm_override, int mode)
+                     const uint32_t perm01[2], const uint32_t *perm2_given, int mode)
 {
     const rmso_config *cfg = X->cfg;
     const int L = cfg->n_labels;
@@ -371,12 +410,6 @@ static int walk_step(const ctx *X, uint64_t w, uint32_t k, walker *s, double n[3
     double f = 1.0;
     double sc = X->s[s->c];
     double rate = X->dtR[mode][s->c];
-    uint32_t perm[4];
-    int have_perm = 0;
-    if (perm_override) {
-        memcpy(perm, perm_override, sizeof(perm));
-        have_perm = 1;
-    }
     for (int ev = 0;; ev++) {
         double d[3] = {n[0] * sc, n[1] * sc, n[2] * sc};
         int best = -1;
@@ -439,11 +472,17 @@ static int walk_step(const ctx *X, uint64_t w, uint32_t k, walker *s, double n[3
             if (T == 0u) {
                 cross = 0;
             } else {
-                if (!have_perm) {
-                    draw(cfg->seed, w, k, TAG_PERM, 0u, perm);
-                    have_perm = 1;
+                uint32_t word;
+                if (ev < 2) {
+                    word = perm01[ev];
+                } else if (perm2_given) {
+                    word = *perm2_given;
+                } else {
+                    uint32_t p4[4];
+                    draw(cfg->seed, w, k, TAG_PERM, 0u, p4);
+                    word = p4[0];
                 }
-                cross = perm[ev] < T;
+                cross = word < T;
             }
         }
         if (cross) {
@@ -523,12 +562,10 @@ static void *run_range(void *arg)
         int r = 0;
         for (int64_t k = 1; k <= cfg->n_steps; k++) {
             double n[3];
-            if (direction(cfg->seed, (uint64_t)w, (uint32_t)k, n)) {
-                J->err |= RMSO_ERR_DIRECTION;
-                n[0] = 0.0; n[1] = 0.0; n[2] = 1.0;
-            }
+            uint32_t perm01[2];
+            direction(cfg->seed, (uint64_t)w, (uint32_t)k, n, perm01);
             int mode = cfg->mode ? cfg->mode[k - 1] : 0;
-            J->err |= walk_step(X, (uint64_t)w, (uint32_t)k, &s, n, NULL, mode);
+            J->err |= walk_step(X, (uint64_t)w, (uint32_t)k, &s, n, perm01, NULL, mode);
             if (cfg->hash) {
                 uint64_t v = (((uint64_t)k & 0xFFFFu) << 48) ^ ((uint64_t)(uint32_t)s.c << 32) ^
                              (uint64_t)flat_index(cfg, s.i);
@@ -680,7 +717,7 @@ void rmso_readout(int64_t n_walkers, int32_t n_shapes, const double *phase, cons
 /* Test hooks (tests only)                                             */
 /* ------------------------------------------------------------------ */
 /* One face walk from a given state with a given direction and given PERM
- * words (bypasses the DIR and PERM draws).  state_i/state_o/c/A are in-out;
+ * words perm[0..2] for the step's events 0..2 (bypasses the random draws).  state_i/state_o/c/A are in-out;
  * n is in-out (reflections flip it).  Returns error bits; events out. */
 int rmso_walk_once(const rmso_config *cfg, int64_t state_i[3], double state_o[3], int32_t *c,
                    double *A, double n[3], const uint32_t perm[4], int32_t mode, int64_t counts[3])
@@ -699,7 +736,7 @@ int rmso_walk_once(const rmso_config *cfg, int64_t state_i[3], double state_o[3]
     }
     s.c = *c;
     s.A = *A;
-    err = walk_step(&X, 0u, 1u, &s, n, perm, mode);
+    err = walk_step(&X, 0u, 1u, &s, n, perm, perm + 2, mode);
     for (int a = 0; a < 3; a++) {
         state_i[a] = s.i[a];
         state_o[a] = s.o[a];
@@ -729,4 +766,12 @@ int rmso_thresholds(const rmso_config *cfg, uint32_t *T_out, double *s_out)
 }
 
 /* The unit direction of step k of walker w (DIR stream). */
-int rmso_direction(uint64_t seed, uint64_t w, uint32_t k, double n[3]) { return direction(seed, w, k, n); }
+int rmso_direction(uint64_t seed, uint64_t w, uint32_t k, double n[3])
+{
+    uint32_t p[2];
+    direction(seed, w, k, n, p);
+    return 0;
+}
+
+/* The unit direction made from two given words. */
+void rmso_direction_from_words(uint32_t x0, uint32_t x1, double n[3]) { direction_from(x0, x1, n); }

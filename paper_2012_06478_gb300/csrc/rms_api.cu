@@ -894,7 +894,6 @@ static rms_status finish(rms_run_handle *r)
     RMS_CUDA(cudaMemcpy(&status, r->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
     if (status & kErrFourthEvent)
         return fail(RMS_E_DEVICE, "a step met a fourth face (some step length >= voxel size)");
-    if (status & kErrDirection) return fail(RMS_E_DEVICE, "direction sampler exhausted its draws");
     if (status) return fail(RMS_E_DEVICE, "device status " + std::to_string(status));
     return RMS_OK;
 }

@@ -30,34 +30,75 @@ __device__ __forceinline__ Real clamp01(Real x)
     return x;
 }
 
-// Sec. 2.2 item 2, the direction: Marsaglia (1972) from two 32-bit words,
-// v = 2u - 1, accept s = v1^2 + v2^2 < 1, n = (2 v1 r, 2 v2 r, 1 - 2 s),
-// r = sqrt(1 - s).
-__device__ __forceinline__ bool marsaglia(uint32_t a, uint32_t b, double n[3])
+// Sec. 2.2 item 2, the direction.  z = 1 - 2u is uniform on [-1, 1] for a
+// uniform point of the sphere (Archimedes); the azimuth is
+// phi = 2 pi (x1 + 1/2) 2^-32.  Its sine and cosine come from Taylor
+// polynomials on [0, pi/4] after an octant reduction in integers, so the FP64
+// form uses only +, * and sqrt -- the same bits as any IEEE machine given the
+// same operation order -- and no warp ever loops on a rejection.
+__device__ __forceinline__ void octant_map(uint32_t oct, double cs, double sn, double &cx, double &sy)
 {
-    const double v1 = 2.0 * u01(a) - 1.0;
-    const double v2 = 2.0 * u01(b) - 1.0;
-    const double s = v1 * v1 + v2 * v2;
-    if (!(s < 1.0)) return false;
-    const double r = sqrt(1.0 - s);
-    n[0] = (2.0 * v1) * r;
-    n[1] = (2.0 * v2) * r;
-    n[2] = 1.0 - 2.0 * s;
-    return true;
+    const bool swap = ((oct + 1u) >> 1) & 1u;  // octants 1, 2, 5, 6
+    const bool negx = ((oct + 2u) >> 2) & 1u;  // octants 2..5
+    const bool negy = (oct >> 2) & 1u;         // octants 4..7
+    const double a = swap ? sn : cs, b = swap ? cs : sn;
+    cx = negx ? -a : a;
+    sy = negy ? -b : b;
 }
 
-// FP32 form of the same sampler: v from the word's signed value.
-__device__ __forceinline__ bool marsaglia(uint32_t a, uint32_t b, float n[3])
+__device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, double n[3])
 {
-    const float v1 = __int2float_rn((int32_t)(a ^ 0x80000000u)) * 0x1p-31f;
-    const float v2 = __int2float_rn((int32_t)(b ^ 0x80000000u)) * 0x1p-31f;
-    const float s = v1 * v1 + v2 * v2;
-    if (!(s < 1.0f)) return false;
-    const float r = sqrtf(1.0f - s);
-    n[0] = (2.0f * v1) * r;
-    n[1] = (2.0f * v2) * r;
-    n[2] = 1.0f - 2.0f * s;
-    return true;
+    const double z = 1.0 - 2.0 * u01(x0);
+    const double r = sqrt((1.0 - z) * (1.0 + z));
+    const uint32_t oct = x1 >> 29;
+    uint32_t m = x1 & 0x1FFFFFFFu;
+    if (oct & 1u) m = 0x1FFFFFFFu - m;
+    const double th = (((double)m + 0.5) * 0x1p-29) * 0.78539816339744830962;
+    const double t = th * th;
+    double ps = 1.0 / 355687428096000.0;
+    ps = -1.0 / 1307674368000.0 + t * ps;
+    ps = 1.0 / 6227020800.0 + t * ps;
+    ps = -1.0 / 39916800.0 + t * ps;
+    ps = 1.0 / 362880.0 + t * ps;
+    ps = -1.0 / 5040.0 + t * ps;
+    ps = 1.0 / 120.0 + t * ps;
+    ps = -1.0 / 6.0 + t * ps;
+    const double sn = th + (th * t) * ps;
+    double pc = 1.0 / 20922789888000.0;
+    pc = -1.0 / 87178291200.0 + t * pc;
+    pc = 1.0 / 479001600.0 + t * pc;
+    pc = -1.0 / 3628800.0 + t * pc;
+    pc = 1.0 / 40320.0 + t * pc;
+    pc = -1.0 / 720.0 + t * pc;
+    pc = 1.0 / 24.0 + t * pc;
+    pc = -1.0 / 2.0 + t * pc;
+    const double cs = 1.0 + t * pc;
+    double cx, sy;
+    octant_map(oct, cs, sn, cx, sy);
+    n[0] = r * cx;
+    n[1] = r * sy;
+    n[2] = z;
+}
+
+// FP32 form of the same sampler (shorter polynomials: truncation below 1e-8).
+__device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, float n[3])
+{
+    const float z = -((float)(int32_t)(x0 ^ 0x80000000u) + 0.5f) * 0x1p-31f;
+    const float r = sqrtf((1.0f - z) * (1.0f + z));
+    const uint32_t oct = x1 >> 29;
+    uint32_t m = x1 & 0x1FFFFFFFu;
+    if (oct & 1u) m = 0x1FFFFFFFu - m;
+    const float th = ((float)m + 0.5f) * (0x1p-29f * 0.785398163f);
+    const float t = th * th;
+    const float sn = th + (th * t) * (-1.0f / 6.0f + t * (1.0f / 120.0f + t * (-1.0f / 5040.0f + t * (1.0f / 362880.0f))));
+    const float cs = 1.0f + t * (-0.5f + t * (1.0f / 24.0f + t * (-1.0f / 720.0f + t * (1.0f / 40320.0f + t * (-1.0f / 3628800.0f)))));
+    const bool swap = ((oct + 1u) >> 1) & 1u;
+    const bool negx = ((oct + 2u) >> 2) & 1u;
+    const bool negy = (oct >> 2) & 1u;
+    const float a = swap ? sn : cs, b = swap ? cs : sn;
+    n[0] = r * (negx ? -a : a);
+    n[1] = r * (negy ? -b : b);
+    n[2] = z;
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -77,15 +118,24 @@ __device__ __forceinline__ void kahan_add(Real &sum, Real &comp, Real x)
 }
 
 // The 22 moment terms at a recording step (Sec. 2.3, narrow-pulse D and K):
-// alpha, alpha dx_i dx_j (i <= j), alpha dx_i dx_j dx_k dx_l (i<=j<=k<=l).
-__device__ __forceinline__ void moment_terms(double al, const double dx[3], double m[kMoments])
+// alpha, alpha dx_i dx_j (i <= j), alpha dx_i dx_j dx_k dx_l (i<=j<=k<=l),
+// each reduced over the warp as soon as it is formed (few live registers);
+// lane 0 of each warp leaves the warp's 22 sums in red[22].
+__device__ __forceinline__ void warp_moments(double al, const double dx[3], double *red)
 {
+    const int lane = threadIdx.x & 31;
     int p = 0;
-    m[p++] = al;
+    double r = warp_sum(al);
+    if (lane == 0) red[p] = r;
+    ++p;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = a; b < 3; ++b) m[p++] = al * dx[a] * dx[b];
+        for (int b = a; b < 3; ++b) {
+            r = warp_sum(al * dx[a] * dx[b]);
+            if (lane == 0) red[p] = r;
+            ++p;
+        }
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -93,7 +143,11 @@ __device__ __forceinline__ void moment_terms(double al, const double dx[3], doub
 #pragma unroll
             for (int c = b; c < 3; ++c)
 #pragma unroll
-                for (int d = c; d < 3; ++d) m[p++] = al * dx[a] * dx[b] * dx[c] * dx[d];
+                for (int d = c; d < 3; ++d) {
+                    r = warp_sum(al * dx[a] * dx[b] * dx[c] * dx[d]);
+                    if (lane == 0) red[p] = r;
+                    ++p;
+                }
 }
 
 // Steps (k_begin, k_end] for every walker of the run.
@@ -161,27 +215,17 @@ walk_kernel(Geometry g, Tables<Real> t, WalkerState<Real> st, RunCtl ctl, int64_
     for (int64_t k = k_begin + 1; k <= k_end; ++k) {
         const uint8_t fl = __ldg(t.flags + (k - 1));
         if (active) {
-            // ---- direction (DIR stream)
+            // ---- direction (one DIR call: words 0, 1 -> direction; words 2, 3 ->
+            //      the Bernoulli words of the step's first two membrane events)
+            const U4 x = draw(ctl.seed, w, (uint32_t)k, kTagDir, 0u);
             Real n[3];
-            bool ok = false;
-            for (uint32_t call = 0; call < 64u && !ok; ++call) {
-                const U4 x = draw(ctl.seed, w, (uint32_t)k, kTagDir, call);
-                ok = marsaglia(x.x, x.y, n) || marsaglia(x.z, x.w, n);
-            }
-            if (!ok) {
-                atomicOr(ctl.status, kErrDirection);
-                n[0] = Real(0);
-                n[1] = Real(0);
-                n[2] = Real(1);
-            }
+            direction_from(x.x, x.y, n);
             // ---- face walk (Sec. 2.2 items 3-4)
             const int mode = t.mode ? (int)__ldg(t.mode + (k - 1)) : 0;
             Real sc = __ldg(t.s + c);
             Real rate = t.any_relax ? __ldg(t.dtR + mode * L + c) : Real(0);
             Real d[3] = {n[0] * sc, n[1] * sc, n[2] * sc};
             Real f = Real(1);
-            bool have_perm = false;
-            U4 perm = U4{0u, 0u, 0u, 0u};
             for (int ev = 0;; ++ev) {
                 int best = -1;
                 Real tbest = Real(0);
@@ -277,11 +321,9 @@ walk_kernel(Geometry g, Tables<Real> t, WalkerState<Real> st, RunCtl ctl, int64_
                     if (T == 0u) {
                         cross = false;
                     } else {
-                        if (!have_perm) {
-                            perm = draw(ctl.seed, w, (uint32_t)k, kTagPerm, 0u);
-                            have_perm = true;
-                        }
-                        const uint32_t word = ev == 0 ? perm.x : (ev == 1 ? perm.y : perm.z);
+                        // third membrane event of a step: word 0 of the step's PERM call
+                        const uint32_t word =
+                            ev == 0 ? x.z : (ev == 1 ? x.w : draw(ctl.seed, w, (uint32_t)k, kTagPerm, 0u).x);
                         cross = word < T;
                     }
                 }
@@ -338,24 +380,15 @@ walk_kernel(Geometry g, Tables<Real> t, WalkerState<Real> st, RunCtl ctl, int64_
         }
         // ---- displacement moments at recording steps (block-uniform branch)
         if (fl & 2u) {
-            double m[kMoments];
+            double dx[3] = {0.0, 0.0, 0.0};
+            double al = 0.0;
             if (active) {
-                double dx[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
                     dx[a] = g.voxel_um * ((double)di[a] + ((double)o[a] - (double)o0[a]));
-                const double al = kF64 ? exp(-(double)A) : exp(-((double)A - (double)Ac));
-                moment_terms(al, dx, m);
-            } else {
-#pragma unroll
-                for (int q = 0; q < kMoments; ++q) m[q] = 0.0;
+                al = kF64 ? exp(-(double)A) : exp(-((double)A - (double)Ac));
             }
-            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-            for (int q = 0; q < kMoments; ++q) {
-                const double r = warp_sum(m[q]);
-                if (lane == 0) s_red[wid][q] = r;
-            }
+            warp_moments(al, dx, s_red[threadIdx.x >> 5]);
             __syncthreads();
             if (threadIdx.x < kMoments) {
                 double acc = 0.0;

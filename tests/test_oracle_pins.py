@@ -148,13 +148,13 @@ def test_cross_into_other_diffusivity_keeps_time_fraction(oracle_lib):
     s1, s2 = ds_of(2.0, 1e-3) / 0.2, ds_of(0.5, 1e-3) / 0.2
     o_x = 1.0 - 0.3 * s1
     i, o, c, A, n, counts, err = oracle_lib.walk_once(wl, [0, 0, 0], [o_x, 0.5, 0.5], 0, [1.0, 0, 0],
-                                                      perm=[0, 0, 0, 0])
+                                                      perm=[0, 0, 0])
     assert err == 0 and c == 1 and list(i) == [1, 0, 0]
     np.testing.assert_allclose(o[0], 0.7 * s2, atol=1e-14)
     np.testing.assert_allclose(A, 0.3 * 1e-3 / 40.0 + 0.7 * 1e-3 / 80.0, rtol=1e-12)
     # the same event with a PERM word above the threshold reflects
     i, o, c, A, n, counts, err = oracle_lib.walk_once(wl, [0, 0, 0], [o_x, 0.5, 0.5], 0, [1.0, 0, 0],
-                                                      perm=[0xFFFFFFFF] * 4)
+                                                      perm=[0xFFFFFFFF] * 3)
     assert c == 0 and list(i) == [0, 0, 0] and n[0] == -1.0
     np.testing.assert_allclose(o[0], 1.0 - 0.7 * s1, atol=1e-14)
 
@@ -224,7 +224,7 @@ def test_single_steps_match_brute_force(oracle_lib):
         v = rng.normal(size=3)
         n0 = v / np.linalg.norm(v)
         o0 = rng.uniform(0, 1, size=3)
-        perm = [int(x) for x in rng.integers(0, 2 ** 32, size=4, dtype=np.uint64)]
+        perm = [int(x) for x in rng.integers(0, 2 ** 32, size=3, dtype=np.uint64)]
         ref = _brute_force_step(lab, T, s, i0, o0, c0, n0, perm)
         times = ref[7]
         if any(abs(x - 1) < 1e-9 for x in times) or any(abs(a - b) < 1e-9 for a in times for b in times
@@ -447,3 +447,23 @@ def test_finite_step_permeability_correction(oracle_lib):
     uncorrected = _exchange_fraction(a, D, kappa / (1 - alpha), n * dt)
     assert expect - uncorrected > 0.015
     assert abs(stay - expect) < Z * math.sqrt(0.25 / W) + 0.003, (stay, expect, uncorrected)
+
+
+def test_direction_sampler_closed_form(oracle_lib):
+    """The direction of words (x0, x1) is (r cos phi, r sin phi, z) with
+    z = 1 - 2 (x0 + 1/2) 2^-32, r = sqrt(1 - z^2), phi = 2 pi (x1 + 1/2) 2^-32
+    (Archimedes: z uniform on [-1, 1] gives a uniform point of the sphere);
+    checked against libm on words covering every octant and its edges."""
+    rng = np.random.default_rng(17)
+    words = list(rng.integers(0, 2 ** 32, size=(3000, 2), dtype=np.uint64))
+    for o in range(8):
+        for m in (0, 1, 0x1FFFFFFE, 0x1FFFFFFF, 0x0FFFFFFF):
+            words.append(np.array([int(rng.integers(0, 2 ** 32)), (o << 29) | m], dtype=np.uint64))
+    words += [np.array([0, 0], np.uint64), np.array([2 ** 32 - 1, 2 ** 32 - 1], np.uint64)]
+    for x0, x1 in words:
+        n = oracle_lib.direction_from_words(int(x0), int(x1))
+        z = 1.0 - 2.0 * (int(x0) + 0.5) * 2.0 ** -32
+        phi = 2 * math.pi * (int(x1) + 0.5) * 2.0 ** -32
+        r = math.sqrt((1 - z) * (1 + z))  # 1 - z and 1 + z are exact
+        np.testing.assert_allclose(n, [r * math.cos(phi), r * math.sin(phi), z], rtol=0, atol=1e-15)
+        assert abs(np.dot(n, n) - 1.0) < 1e-15
