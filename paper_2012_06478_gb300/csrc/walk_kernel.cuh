@@ -225,63 +225,9 @@ walk_kernel(Geometry g, Tables<Real> t, WalkerState<Real> st, RunCtl ctl, int64_
             Real sc = __ldg(t.s + c);
             Real rate = t.any_relax ? __ldg(t.dtR + mode * L + c) : Real(0);
             Real d[3] = {n[0] * sc, n[1] * sc, n[2] * sc};
-            Real f = Real(1);
-            for (int ev = 0;; ++ev) {
-                int best = -1;
-                Real tbest = Real(0);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    Real dist, ad;
-                    bool cand = true;
-                    if (d[a] > Real(0)) {
-                        dist = Real(1) - o[a];
-                        ad = d[a];
-                    } else if (d[a] < Real(0)) {
-                        dist = o[a];
-                        ad = -d[a];
-                    } else {
-                        cand = false;
-                        dist = ad = Real(1);
-                    }
-                    if (cand && dist < f * ad) {
-                        const Real tt = dist / ad;
-                        if (best < 0 || tt < tbest) {
-                            best = a;
-                            tbest = tt;
-                        }
-                    }
-                }
-                if (best < 0 || ev == 3) {
-                    if (best >= 0) atomicOr(ctl.status, kErrFourthEvent);
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) o[a] = clamp01(o[a] + f * d[a]);
-                    if (t.any_relax) {
-                        if (kF64)
-                            A = A + f * rate;
-                        else
-                            kahan_add(A, Ac, f * rate);
-                    }
-                    break;
-                }
-                const Real tt = tbest < f ? tbest : f;
-                bool up = false;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (a == best) {
-                        up = d[a] > Real(0);
-                        o[a] = up ? Real(1) : Real(0);
-                    } else {
-                        o[a] = clamp01(o[a] + tt * d[a]);
-                    }
-                }
-                if (t.any_relax) {
-                    if (kF64)
-                        A = A + tt * rate;
-                    else
-                        kahan_add(A, Ac, tt * rate);
-                }
-                f = f - tt;
-                // the voxel across the face
+            // A face event on axis `best` moving up/down: look up the voxel across
+            // it and decide between crossing and reflection.
+            auto face = [&](int best, bool up, int ev) -> bool {
                 int32_t coord = 0, Nb = 1, sb = 1, pb = 1;
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
@@ -310,7 +256,7 @@ walk_kernel(Geometry g, Tables<Real> t, WalkerState<Real> st, RunCtl ctl, int64_
                         nv = v + (Nb - 1) * sb;
                     }
                 }
-                int32_t c2 = wall ? -1 : (int32_t)__ldg(g.labels + nv);
+                const int32_t c2 = wall ? -1 : (int32_t)__ldg(g.labels + nv);
                 bool cross;
                 if (c2 == c) {
                     cross = true;
@@ -338,10 +284,8 @@ walk_kernel(Geometry g, Tables<Real> t, WalkerState<Real> st, RunCtl ctl, int64_
                     v = nv;
                     if (c2 != c) {
                         c = c2;
-                        sc = __ldg(t.s + c);
                         if (t.any_relax) rate = __ldg(t.dtR + mode * L + c);
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) d[a] = n[a] * sc;
+                        return true;  // the caller switches to the new label's step length
                     }
                 } else {
 #pragma unroll
@@ -351,6 +295,121 @@ walk_kernel(Geometry g, Tables<Real> t, WalkerState<Real> st, RunCtl ctl, int64_
                             d[a] = -d[a];
                         }
                 }
+                return false;
+            };
+            if constexpr (kF64) {
+                // Plain form: the reference's formulation, operation for operation.
+                // Remaining fraction f; candidates dist_a < f |d_a| at t_a = dist_a/|d_a|.
+                Real f = Real(1);
+                for (int ev = 0;; ++ev) {
+                    int best = -1;
+                    Real tbest = Real(0);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        Real dist, ad;
+                        bool cand = true;
+                        if (d[a] > Real(0)) {
+                            dist = Real(1) - o[a];
+                            ad = d[a];
+                        } else if (d[a] < Real(0)) {
+                            dist = o[a];
+                            ad = -d[a];
+                        } else {
+                            cand = false;
+                            dist = ad = Real(1);
+                        }
+                        if (cand && dist < f * ad) {
+                            const Real tt = dist / ad;
+                            if (best < 0 || tt < tbest) {
+                                best = a;
+                                tbest = tt;
+                            }
+                        }
+                    }
+                    if (best < 0 || ev == 3) {
+                        if (best >= 0) atomicOr(ctl.status, kErrFourthEvent);
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) o[a] = clamp01(o[a] + f * d[a]);
+                        if (t.any_relax) A = A + f * rate;
+                        break;
+                    }
+                    const Real tt = tbest < f ? tbest : f;
+                    bool up = false;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        if (a == best) {
+                            up = d[a] > Real(0);
+                            o[a] = up ? Real(1) : Real(0);
+                        } else {
+                            o[a] = clamp01(o[a] + tt * d[a]);
+                        }
+                    }
+                    if (t.any_relax) A = A + tt * rate;
+                    f = f - tt;
+                    if (face(best, up, ev)) {
+                        sc = __ldg(t.s + c);
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) d[a] = n[a] * sc;
+                    }
+                }
+            } else {
+                // Precision form.  Each axis meets at most one face per step (s_c < 1:
+                // the corner reflector), and events on one axis leave the others'
+                // motion unchanged, so the three face times are found once, from the
+                // start of the step; events are then taken in time order, and only a
+                // change of step length (crossing into another D) rescales the
+                // remaining times.
+                Real T[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const Real ad = fabsf(d[a]);
+                    const Real dist = d[a] > Real(0) ? Real(1) - o[a] : o[a];
+                    T[a] = (dist < ad) ? __fdividef(dist, ad) : Real(2);
+                }
+                Real tau = Real(0);
+#pragma unroll 1
+                for (int ev = 0; ev < 3; ++ev) {
+                    int best = 0;
+                    Real tmin = T[0];
+                    if (T[1] < tmin) {
+                        best = 1;
+                        tmin = T[1];
+                    }
+                    if (T[2] < tmin) {
+                        best = 2;
+                        tmin = T[2];
+                    }
+                    if (!(tmin < Real(1))) break;
+                    tmin = fmaxf(tmin, tau);
+                    const Real dtt = tmin - tau;
+                    bool up = false;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        if (a == best) {
+                            up = d[a] > Real(0);
+                            o[a] = up ? Real(1) : Real(0);
+                            T[a] = Real(2);
+                        } else {
+                            o[a] = clamp01(o[a] + dtt * d[a]);
+                        }
+                    }
+                    if (t.any_relax) kahan_add(A, Ac, dtt * rate);
+                    tau = tmin;
+                    if (face(best, up, ev)) {
+                        const Real sn = __ldg(t.s + c);
+                        const Real ratio = __fdividef(sc, sn);
+                        sc = sn;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            d[a] = n[a] * sc;
+                            if (T[a] < Real(1)) T[a] = tau + (T[a] - tau) * ratio;
+                        }
+                    }
+                }
+                const Real rem = Real(1) - tau;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) o[a] = clamp01(o[a] + rem * d[a]);
+                if (t.any_relax) kahan_add(A, Ac, rem * rate);
             }
             if (HASH) {
                 const uint64_t x = (((uint64_t)k & 0xFFFFu) << 48) ^ ((uint64_t)(uint32_t)c << 32) ^
