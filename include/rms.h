@@ -189,6 +189,54 @@ rms_status rms_destroy_run(rms_run_handle *run);
 rms_status rms_run_step_time_ms(rms_run_handle *run, float *ms);
 
 /* ------------------------------------------------------------------ */
+/* Serving: continuous batching of simulation requests.                */
+/* Not in the paper (which runs one simulation per GPU, Sec. 2.1.5):   */
+/* requests on resident substrates arrive at any time, are admitted as */
+/* request slots and device memory free up, and every active request   */
+/* advances in the same batched kernel launches, tick by tick.         */
+/* ------------------------------------------------------------------ */
+typedef struct rms_server rms_server;
+
+typedef struct {
+    int64_t memory_budget_bytes; /* device memory for the walker state of admitted requests (0: 8 GiB);
+                                    a request is admitted when it fits (or when nothing else runs) */
+    int32_t max_active;          /* requests admitted at once, 1..1024 (0: 64) */
+    int32_t steps_per_tick;      /* steps every active request advances per tick (0: 256) */
+} rms_server_config;
+
+/* Start the scheduler thread on the current device. */
+rms_status rms_server_create(const rms_server_config *cfg, rms_server **out);
+
+/* Queue a request: n_walkers walkers of `seq` (its substrate stays resident;
+ * both must outlive the request -- destroying them returns RMS_E_BUSY
+ * meanwhile), Philox key `seed`, RMS_FP64 or RMS_FP32.  Returns at once with
+ * a ticket.  The result equals rms_run's for the same arguments. */
+rms_status rms_server_submit(rms_server *srv, rms_sequence *seq, int64_t n_walkers, uint64_t seed,
+                             int32_t precision, int64_t *ticket);
+
+/* RMS_OK when the ticket's request has finished (or failed, or was
+ * cancelled), RMS_E_NOT_READY otherwise. */
+rms_status rms_server_poll(rms_server *srv, int64_t ticket);
+
+/* Wait up to timeout_ms (< 0: no limit) and copy the result to host memory
+ * (layouts as rms_read_signal; any pointer may be NULL); the ticket is then
+ * released.  RMS_E_TIMEOUT (ticket kept), RMS_E_CANCELLED, RMS_E_DEVICE. */
+rms_status rms_server_wait(rms_server *srv, int64_t ticket, int64_t timeout_ms, double *S_re, double *S_im,
+                           double *moments, double *alpha_sum);
+
+/* Withdraw a queued or running request (a finishing one still completes). */
+rms_status rms_server_cancel(rms_server *srv, int64_t ticket);
+
+/* 11 doubles: p50, p99 and mean request latency (ms, submit to result),
+ * walker-steps/s (all requests, first submit to last completion), completed,
+ * in flight, queued, peak in flight, ticks, graph updates, graph
+ * instantiations. */
+rms_status rms_server_stats(rms_server *srv, double *out);
+
+/* Cancel what is queued or running, stop the thread, free everything. */
+rms_status rms_server_destroy(rms_server *srv);
+
+/* ------------------------------------------------------------------ */
 /* Signal read-out that allocates nothing.  The paper has no           */
 /* counterpart: this is a service for callers that may not allocate    */
 /* device memory at the point of the call -- for example a serving     */

@@ -46,6 +46,10 @@ class SequenceDesc(C.Structure):
                 ("b", C.c_void_p), ("n_rec", C.c_int32), ("rec_steps", C.c_void_p)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("memory_budget_bytes", C.c_int64), ("max_active", C.c_int32), ("steps_per_tick", C.c_int32)]
+
+
 class RunDesc(C.Structure):
     _fields_ = [("n_walkers", C.c_int64), ("walker_begin", C.c_int64), ("seed", C.c_uint64),
                 ("precision", C.c_int32), ("flags", C.c_uint32), ("steps_per_launch", C.c_int32),
@@ -68,6 +72,14 @@ SIGNATURES = {
     "rms_read_walkers": ([C.c_void_p] + [C.c_void_p] * 8, C.c_int),
     "rms_destroy_run": ([C.c_void_p], C.c_int),
     "rms_run_step_time_ms": ([C.c_void_p, C.POINTER(C.c_float)], C.c_int),
+    "rms_server_create": ([C.POINTER(ServerConfig), C.POINTER(C.c_void_p)], C.c_int),
+    "rms_server_submit": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64, C.c_int32, C.POINTER(C.c_int64)],
+                          C.c_int),
+    "rms_server_poll": ([C.c_void_p, C.c_int64], C.c_int),
+    "rms_server_wait": ([C.c_void_p, C.c_int64, C.c_int64] + [C.c_void_p] * 4, C.c_int),
+    "rms_server_cancel": ([C.c_void_p, C.c_int64], C.c_int),
+    "rms_server_stats": ([C.c_void_p, C.c_void_p], C.c_int),
+    "rms_server_destroy": ([C.c_void_p], C.c_int),
     "rms_readout_noalloc": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
                              C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 }

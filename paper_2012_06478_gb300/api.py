@@ -22,7 +22,7 @@ from ._lib import RMS_FP32, RMS_FP64, RMS_TRAJ_HASH, RmsError, check
 __all__ = ["rms_create_substrate", "rms_set_sequence", "rms_run", "rms_read_signal", "rms_read_walkers",
            "rms_cancel", "rms_run_query", "rms_destroy_run", "rms_destroy_sequence", "rms_destroy_substrate",
            "rms_sequence_bvalues", "rms_run_step_time_ms", "simulate", "current_stream",
-           "RMS_FP32", "RMS_FP64", "RMS_TRAJ_HASH", "RmsError", "MOMENT_NAMES"]
+           "RMS_FP32", "RMS_FP64", "RMS_TRAJ_HASH", "RmsError", "MOMENT_NAMES", "Server"]
 
 MOMENT_NAMES = ["1", "xx", "xy", "xz", "yy", "yz", "zz", "xxxx", "xxxy", "xxxz", "xxyy", "xxyz", "xxzz", "xyyy",
                 "xyyz", "xyzz", "xzzz", "yyyy", "yyyz", "yyzz", "yzzz", "zzzz"]
@@ -255,3 +255,58 @@ def simulate(wl, precision: int = RMS_FP64, n_walkers: Optional[int] = None, see
     seq.close()
     sub.close()
     return res
+
+
+class Server:
+    """The continuous-batching serving loop (rms_server_* in include/rms.h)."""
+
+    STATS = ("p50_ms", "p99_ms", "mean_ms", "walker_steps_per_s", "completed", "in_flight", "queued",
+             "peak_in_flight", "ticks", "graph_updates", "graph_instantiations")
+
+    def __init__(self, memory_budget_bytes: int = 0, max_active: int = 0, steps_per_tick: int = 0):
+        cfg = L.ServerConfig(int(memory_budget_bytes), int(max_active), int(steps_per_tick))
+        h = C.c_void_p()
+        check(L.lib.rms_server_create(C.byref(cfg), C.byref(h)))
+        self.handle = h
+        self._shapes = {}
+
+    def submit(self, seq: Sequence, n_walkers: int, seed: int, precision: int = RMS_FP64) -> int:
+        t = C.c_int64()
+        check(L.lib.rms_server_submit(self.handle, seq.handle, int(n_walkers), int(seed), int(precision),
+                                      C.byref(t)))
+        self._shapes[t.value] = seq
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        return check(L.lib.rms_server_poll(self.handle, ticket), allow=(L.RMS_OK, L.RMS_E_NOT_READY)) == L.RMS_OK
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """(S complex (n_shapes, n_dirs, n_b), moments (n_rec, 22), alpha_sum)."""
+        q = self._shapes[ticket]
+        n = q.n_shapes * q.n_dirs * q.n_b
+        re, im = np.zeros(n), np.zeros(n)
+        mom = np.zeros((q.n_rec, 22))
+        asum = np.zeros(1)
+        check(L.lib.rms_server_wait(self.handle, ticket, int(timeout_ms), re.ctypes.data, im.ctypes.data,
+                                    mom.ctypes.data if q.n_rec else None, asum.ctypes.data))
+        del self._shapes[ticket]
+        return (re + 1j * im).reshape(q.n_shapes, q.n_dirs, q.n_b), mom, float(asum[0])
+
+    def cancel(self, ticket: int) -> None:
+        check(L.lib.rms_server_cancel(self.handle, ticket))
+
+    def stats(self) -> dict:
+        out = np.zeros(11)
+        check(L.lib.rms_server_stats(self.handle, out.ctypes.data))
+        return dict(zip(self.STATS, out.tolist()))
+
+    def close(self):
+        if self.handle:
+            check(L.lib.rms_server_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
           "--expt-relaxed-constexpr"]
 UNITS = [("rms_api.cu", ["-fmad=false"]), ("walk_fp64.cu", ["-fmad=false"]), ("walk_fp32.cu", ["-fmad=true"]),
-         ("rms_noalloc.cu", ["-fmad=false"])]
+         ("rms_noalloc.cu", ["-fmad=false"]), ("rms_serve.cu", ["-fmad=false"])]
 
 
 def _sources():

@@ -16,6 +16,7 @@
 
 #include "../../include/rms.h"
 #include "rms_device.cuh"
+#include "rms_handles.h"
 #include "rms_internal.h"
 
 using namespace rms;
@@ -24,19 +25,12 @@ using namespace rms;
 
 static thread_local std::string g_last_error;
 
-static rms_status fail(rms_status st, const std::string &msg)
+rms_status rms::fail(rms_status st, const std::string &msg)
 {
     g_last_error = msg;
     return st;
 }
 
-#define RMS_CUDA(call)                                                                            \
-    do {                                                                                          \
-        cudaError_t e_ = (call);                                                                  \
-        if (e_ != cudaSuccess)                                                                    \
-            return fail(e_ == cudaErrorMemoryAllocation ? RMS_E_OOM : RMS_E_CUDA,                 \
-                        std::string(#call) + ": " + cudaGetErrorString(e_));                     \
-    } while (0)
 
 void rms::set_last_error(const char *msg) { g_last_error = msg; }
 
@@ -44,57 +38,6 @@ extern "C" int rms_version(void) { return 10000; }
 extern "C" const char *rms_last_error(void) { return g_last_error.c_str(); }
 
 // ------------------------------------------------------------------ handles
-
-struct rms_substrate {
-    int device = 0;
-    int32_t nx = 0, ny = 0, nz = 0;
-    double voxel_um = 0;
-    int32_t periodic[3] = {1, 1, 1};
-    int32_t L = 0;
-    std::vector<double> D, T2, T1, kappa;
-    std::vector<uint8_t> dead;
-    uint16_t *d_labels = nullptr;
-    double *d_D = nullptr, *d_T2 = nullptr, *d_T1 = nullptr, *d_kappa = nullptr;
-    uint8_t *d_dead = nullptr;
-    int32_t *d_ok = nullptr;  // raster list of non-dead voxels (nullptr: none dead)
-    int64_t n_ok = 0;
-    std::atomic<int> refs{0};
-};
-
-struct rms_sequence {
-    rms_substrate *sub = nullptr;
-    double dt = 0;
-    int64_t n_steps = 0;
-    int32_t S = 0, n_dirs = 0, n_b = 0, n_rec = 0;
-    int32_t any_relax = 0;
-    int32_t has_mode = 0;
-    double *d_s64 = nullptr, *d_dtR64 = nullptr, *d_wG64 = nullptr;
-    float *d_s32 = nullptr, *d_dtR32 = nullptr, *d_wG32 = nullptr;
-    uint32_t *d_T = nullptr;
-    uint8_t *d_flags = nullptr, *d_mode = nullptr;
-    int32_t *d_rec_of = nullptr;
-    double *d_dirs = nullptr, *d_b = nullptr, *d_bs = nullptr, *d_q = nullptr;
-    std::atomic<int> refs{0};
-};
-
-struct rms_run_handle {
-    rms_sequence *seq = nullptr;
-    int64_t W = 0, w_begin = 0;
-    uint64_t seed = 0;
-    int32_t precision = RMS_FP64;
-    uint32_t flags = 0;
-    cudaStream_t stream = nullptr;
-    int32_t n_blocks = 0;
-    char *d_state = nullptr;  // one allocation for the walker state
-    WalkerState<double> st64{};
-    WalkerState<float> st32{};
-    double *d_mom_partial = nullptr, *d_mom = nullptr;
-    double *d_ro_partial = nullptr, *d_S = nullptr;  // S: [combo][2] + alpha sum
-    int32_t *d_status = nullptr;
-    int32_t *h_cancel = nullptr, *d_cancel = nullptr;
-    cudaEvent_t ev_start = nullptr, ev_end = nullptr;
-    int32_t n_combo = 0, n_chunks = 0;
-};
 
 // ------------------------------------------------------------------ set-up kernels
 
@@ -453,11 +396,6 @@ static rms_status upload(T **dst, const T *src, size_t n, cudaStream_t s, bool s
     return RMS_OK;
 }
 
-#define RMS_TRY(expr)                 \
-    do {                              \
-        rms_status st_ = (expr);      \
-        if (st_ < 0) return st_;      \
-    } while (0)
 
 static void free_substrate(rms_substrate *s, cudaStream_t st)
 {
@@ -719,7 +657,7 @@ extern "C" rms_status rms_destroy_sequence(rms_sequence *q)
 // ------------------------------------------------------------------ run
 
 template <typename Real>
-static size_t layout_state(WalkerState<Real> &st, char *base, int64_t W, int S, bool hash, bool f32)
+size_t rms::layout_state(WalkerState<Real> &st, char *base, int64_t W, int S, bool hash, bool f32)
 {
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -741,35 +679,74 @@ static size_t layout_state(WalkerState<Real> &st, char *base, int64_t W, int S, 
 }
 
 template <typename Real>
-static rms_status enqueue_run(rms_run_handle *r, const WalkerState<Real> &st, const Tables<Real> &t, int32_t spl)
+ReqDesc<Real> rms::run_desc(rms_run_handle *r)
 {
     rms_sequence *q = r->seq;
     rms_substrate *sub = q->sub;
-    cudaStream_t s = r->stream;
-    const bool hash = (r->flags & RMS_TRAJ_HASH) != 0;
-    Geometry g{sub->d_labels, sub->nx, sub->ny, sub->nz, sub->periodic[0], sub->periodic[1], sub->periodic[2],
-               sub->voxel_um};
-    RunCtl ctl{};
-    ctl.seed = r->seed;
-    ctl.w_begin = r->w_begin;
-    ctl.n_walkers = r->W;
-    ctl.n_steps = q->n_steps;
-    ctl.n_shapes = q->S;
-    ctl.n_rec = q->n_rec;
-    ctl.status = r->d_status;
-    ctl.cancel = r->d_cancel;
-    ctl.mom_partial = r->d_mom_partial;
-    ctl.n_blocks = r->n_blocks;
-    const unsigned ib = (unsigned)((r->W + 255) / 256);
-    init_kernel<Real><<<ib, 256, 0, s>>>(g, sub->d_ok, sub->n_ok, st, ctl, hash);
-    RMS_CUDA(cudaGetLastError());
-    RMS_CUDA(cudaEventRecord(r->ev_start, s));
-    const dim3 grid((unsigned)r->n_blocks);
-    for (int64_t k0 = 0; k0 < q->n_steps; k0 += spl) {
-        const int64_t k1 = std::min<int64_t>(q->n_steps, k0 + spl);
-        RMS_CUDA(launch_walk<Real>(q->S, hash, grid, s, g, t, st, ctl, k0, k1));
+    ReqDesc<Real> d{};
+    d.g = Geometry{sub->d_labels, sub->nx, sub->ny, sub->nz, sub->periodic[0], sub->periodic[1], sub->periodic[2],
+                   sub->voxel_um};
+    if constexpr (std::is_same<Real, float>::value) {
+        d.t = Tables<float>{q->d_s32, q->d_dtR32, q->d_T, sub->L, q->d_wG32, q->d_flags, q->d_rec_of, q->d_mode,
+                            q->any_relax};
+        d.st = r->st32;
+    } else {
+        d.t = Tables<double>{q->d_s64, q->d_dtR64, q->d_T, sub->L, q->d_wG64, q->d_flags, q->d_rec_of, q->d_mode,
+                             q->any_relax};
+        d.st = r->st64;
     }
-    RMS_CUDA(cudaEventRecord(r->ev_end, s));
+    d.ctl.seed = r->seed;
+    d.ctl.w_begin = r->w_begin;
+    d.ctl.n_walkers = r->W;
+    d.ctl.n_steps = q->n_steps;
+    d.ctl.n_shapes = q->S;
+    d.ctl.n_rec = q->n_rec;
+    d.ctl.status = r->d_status;
+    d.ctl.cancel = r->d_cancel;
+    d.ctl.mom_partial = r->d_mom_partial;
+    d.ctl.n_blocks = r->n_blocks;
+    return d;
+}
+template ReqDesc<float> rms::run_desc<float>(rms_run_handle *);
+template ReqDesc<double> rms::run_desc<double>(rms_run_handle *);
+
+template <typename Real>
+static rms_status init_impl(rms_run_handle *r)
+{
+    const ReqDesc<Real> d = run_desc<Real>(r);
+    const unsigned ib = (unsigned)((r->W + 255) / 256);
+    init_kernel<Real><<<ib, 256, 0, r->stream>>>(d.g, r->seq->sub->d_ok, r->seq->sub->n_ok, d.st, d.ctl,
+                                                  (r->flags & RMS_TRAJ_HASH) != 0);
+    RMS_CUDA(cudaGetLastError());
+    return RMS_OK;
+}
+
+rms_status rms::run_init(rms_run_handle *r)
+{
+    return r->precision == RMS_FP32 ? init_impl<float>(r) : init_impl<double>(r);
+}
+
+template <typename Real>
+static rms_status walk_impl(rms_run_handle *r, int64_t k0, int64_t k1)
+{
+    const ReqDesc<Real> d = run_desc<Real>(r);
+    RMS_CUDA(launch_walk<Real>(r->seq->S, (r->flags & RMS_TRAJ_HASH) != 0, dim3((unsigned)r->n_blocks), r->stream,
+                               d.g, d.t, d.st, d.ctl, k0, k1));
+    return RMS_OK;
+}
+
+rms_status rms::run_walk(rms_run_handle *r, int64_t k0, int64_t k1)
+{
+    return r->precision == RMS_FP32 ? walk_impl<float>(r, k0, k1) : walk_impl<double>(r, k0, k1);
+}
+
+// Moment sums, the read-out and the normalisation, enqueued on the run's stream.
+template <typename Real>
+static rms_status finalize_impl(rms_run_handle *r)
+{
+    rms_sequence *q = r->seq;
+    cudaStream_t s = r->stream;
+    const WalkerState<Real> st = run_desc<Real>(r).st;
     if (q->n_rec > 0) {
         moments_reduce_kernel<<<(q->n_rec * kMoments + 127) / 128, 128, 0, s>>>(r->d_mom_partial, q->n_rec,
                                                                                 r->n_blocks, r->d_mom);
@@ -785,19 +762,40 @@ static rms_status enqueue_run(rms_run_handle *r, const WalkerState<Real> &st, co
     return RMS_OK;
 }
 
-static void free_run(rms_run_handle *r)
+rms_status rms::run_finalize(rms_run_handle *r)
+{
+    return r->precision == RMS_FP32 ? finalize_impl<float>(r) : finalize_impl<double>(r);
+}
+
+void rms::run_free(rms_run_handle *r, bool sync)
 {
     cudaStream_t s = r->stream;
     void *p[] = {r->d_state, r->d_mom_partial, r->d_mom, r->d_ro_partial, r->d_S, r->d_status};
     for (void *x : p)
         if (x) cudaFreeAsync(x, s);
-    cudaStreamSynchronize(s);
+    if (sync || r->h_cancel) cudaStreamSynchronize(s);
     if (r->h_cancel) cudaFreeHost(r->h_cancel);
     if (r->ev_start) cudaEventDestroy(r->ev_start);
     if (r->ev_end) cudaEventDestroy(r->ev_end);
 }
 
-static rms_status run_impl(rms_run_handle *r, int32_t spl)
+size_t rms::run_state_bytes(const rms_sequence *q, int64_t W, int32_t precision, uint32_t flags)
+{
+    WalkerState<double> s64{};
+    WalkerState<float> s32{};
+    const bool hash = (flags & RMS_TRAJ_HASH) != 0;
+    const int64_t nb = (W + kWalkBlockSize - 1) / kWalkBlockSize;
+    const int64_t nc = (W + kRoChunk - 1) / kRoChunk;
+    const int64_t ncombo = (int64_t)q->S * q->n_dirs * q->n_b;
+    size_t b = precision == RMS_FP32 ? layout_state<float>(s32, nullptr, W, q->S, hash, true)
+                                     : layout_state<double>(s64, nullptr, W, q->S, hash, false);
+    b += sizeof(double) * ((size_t)std::max(q->n_rec, 1) * nb * kMoments + (size_t)std::max(q->n_rec, 1) * kMoments +
+                           2 * (size_t)(ncombo + 1) * nc + 2 * (size_t)(ncombo + 1));
+    return b;
+}
+
+// Allocate the run's device memory (stream-ordered) and lay out the state.
+rms_status rms::run_setup(rms_run_handle *r, bool with_cancel_and_events)
 {
     rms_sequence *q = r->seq;
     cudaStream_t s = r->stream;
@@ -820,19 +818,25 @@ static rms_status run_impl(rms_run_handle *r, int32_t spl)
     RMS_CUDA(cudaMallocAsync((void **)&r->d_S, sizeof(double) * 2 * (r->n_combo + 1), s));
     RMS_CUDA(cudaMallocAsync((void **)&r->d_status, sizeof(int32_t), s));
     RMS_CUDA(cudaMemsetAsync(r->d_status, 0, sizeof(int32_t), s));
-    RMS_CUDA(cudaHostAlloc((void **)&r->h_cancel, sizeof(int32_t), cudaHostAllocMapped));
-    *r->h_cancel = 0;
-    RMS_CUDA(cudaHostGetDevicePointer((void **)&r->d_cancel, r->h_cancel, 0));
-    RMS_CUDA(cudaEventCreate(&r->ev_start));
-    RMS_CUDA(cudaEventCreate(&r->ev_end));
-    if (f32) {
-        Tables<float> t{q->d_s32, q->d_dtR32, q->d_T, q->sub->L, q->d_wG32, q->d_flags, q->d_rec_of, q->d_mode,
-                        q->any_relax};
-        return enqueue_run<float>(r, r->st32, t, spl);
+    if (with_cancel_and_events) {
+        RMS_CUDA(cudaHostAlloc((void **)&r->h_cancel, sizeof(int32_t), cudaHostAllocMapped));
+        *r->h_cancel = 0;
+        RMS_CUDA(cudaHostGetDevicePointer((void **)&r->d_cancel, r->h_cancel, 0));
+        RMS_CUDA(cudaEventCreate(&r->ev_start));
+        RMS_CUDA(cudaEventCreate(&r->ev_end));
     }
-    Tables<double> t{q->d_s64, q->d_dtR64, q->d_T, q->sub->L, q->d_wG64, q->d_flags, q->d_rec_of, q->d_mode,
-                     q->any_relax};
-    return enqueue_run<double>(r, r->st64, t, spl);
+    return RMS_OK;
+}
+
+static rms_status run_impl(rms_run_handle *r, int32_t spl)
+{
+    RMS_TRY(run_setup(r, true));
+    RMS_TRY(run_init(r));
+    RMS_CUDA(cudaEventRecord(r->ev_start, r->stream));
+    for (int64_t k0 = 0; k0 < r->seq->n_steps; k0 += spl)
+        RMS_TRY(run_walk(r, k0, std::min<int64_t>(r->seq->n_steps, k0 + spl)));
+    RMS_CUDA(cudaEventRecord(r->ev_end, r->stream));
+    return run_finalize(r);
 }
 
 extern "C" rms_status rms_run(rms_sequence *q, const rms_run_desc *d, rms_run_handle **out)
@@ -861,7 +865,7 @@ extern "C" rms_status rms_run(rms_sequence *q, const rms_run_desc *d, rms_run_ha
     }
     rms_status st = run_impl(r, spl);
     if (st < 0) {
-        free_run(r);
+        run_free(r, true);
         delete r;
         return st;
     }
@@ -971,7 +975,7 @@ extern "C" rms_status rms_destroy_run(rms_run_handle *r)
 {
     if (!r) return RMS_OK;
     cudaStreamSynchronize(r->stream);
-    free_run(r);
+    run_free(r, true);
     r->seq->refs.fetch_sub(1);
     delete r;
     return RMS_OK;

@@ -106,4 +106,21 @@ struct RunCtl {
     int32_t n_blocks;
 };
 
+// One request of a batched launch: everything the walk needs.
+template <typename Real>
+struct ReqDesc {
+    Geometry g;
+    Tables<Real> t;
+    WalkerState<Real> st;
+    RunCtl ctl;
+};
+
+// One block of a batched launch: block `block` of request `req`, steps (k0, k1].
+struct BlockTask {
+    int32_t req;
+    int32_t pad;
+    int64_t block;
+    int64_t k0, k1;
+};
+
 }  // namespace rms

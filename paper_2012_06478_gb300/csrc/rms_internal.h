@@ -19,6 +19,14 @@ extern template cudaError_t launch_walk<float>(int, bool, dim3, cudaStream_t, co
                                                const Tables<float> &, const WalkerState<float> &,
                                                const RunCtl &, int64_t, int64_t);
 
+template <typename Real>
+cudaError_t launch_walk_batched(int ns_bucket, int32_t n_tasks, cudaStream_t stream, const ReqDesc<Real> *reqs,
+                                const BlockTask *tasks);
+extern template cudaError_t launch_walk_batched<double>(int, int32_t, cudaStream_t, const ReqDesc<double> *,
+                                                        const BlockTask *);
+extern template cudaError_t launch_walk_batched<float>(int, int32_t, cudaStream_t, const ReqDesc<float> *,
+                                                       const BlockTask *);
+
 int walk_block_size();
 
 // Message returned by rms_last_error() on the calling thread.

@@ -8,4 +8,6 @@ namespace rms {
 template cudaError_t launch_walk<float>(int, bool, dim3, cudaStream_t, const Geometry &,
                                         const Tables<float> &, const WalkerState<float> &,
                                         const RunCtl &, int64_t, int64_t);
+template cudaError_t launch_walk_batched<float>(int, int32_t, cudaStream_t, const ReqDesc<float> *,
+                                               const BlockTask *);
 }  // namespace rms

@@ -150,11 +150,11 @@ __device__ __forceinline__ void warp_moments(double al, const double dx[3], doub
                 }
 }
 
-// Steps (k_begin, k_end] for every walker of the run.
+// Steps (k_begin, k_end] for the kWalkBlock walkers of block `block` of a
+// run (walkers block*kWalkBlock ...), one walker per thread.
 template <typename Real, int NS, bool HASH>
-__global__ void __launch_bounds__(kWalkBlock)
-walk_kernel(Geometry g, Tables<Real> t, WalkerState<Real> st, RunCtl ctl, int64_t k_begin,
-            int64_t k_end)
+__device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real> &t, const WalkerState<Real> &st,
+                                           const RunCtl &ctl, int64_t block, int64_t k_begin, int64_t k_end)
 {
     constexpr bool kF64 = std::is_same<Real, double>::value;
     __shared__ int32_t s_cancel;
@@ -163,7 +163,7 @@ walk_kernel(Geometry g, Tables<Real> t, WalkerState<Real> st, RunCtl ctl, int64_
     __syncthreads();
     if (s_cancel) return;
 
-    const int64_t li = (int64_t)blockIdx.x * kWalkBlock + threadIdx.x;
+    const int64_t li = block * kWalkBlock + threadIdx.x;
     const bool active = li < ctl.n_walkers;
     const uint64_t w = (uint64_t)(ctl.w_begin + li);
     const int32_t N[3] = {g.nx, g.ny, g.nz};
@@ -454,7 +454,7 @@ walk_kernel(Geometry g, Tables<Real> t, WalkerState<Real> st, RunCtl ctl, int64_
 #pragma unroll
                 for (int ww = 0; ww < kWalkWarps; ++ww) acc += s_red[ww][threadIdx.x];
                 const int32_t r = __ldg(t.rec_of + (k - 1));
-                ctl.mom_partial[((int64_t)r * ctl.n_blocks + blockIdx.x) * kMoments + threadIdx.x] = acc;
+                ctl.mom_partial[((int64_t)r * ctl.n_blocks + block) * kMoments + threadIdx.x] = acc;
             }
             __syncthreads();
         }
@@ -479,6 +479,49 @@ walk_kernel(Geometry g, Tables<Real> t, WalkerState<Real> st, RunCtl ctl, int64_
                 }
         if (HASH) st.hash[li] = h;
     }
+}
+
+// One run: block b of the grid advances walkers b*kWalkBlock ... of the run.
+template <typename Real, int NS, bool HASH>
+__global__ void __launch_bounds__(kWalkBlock)
+walk_kernel(Geometry g, Tables<Real> t, WalkerState<Real> st, RunCtl ctl, int64_t k_begin, int64_t k_end)
+{
+    walk_block<Real, NS, HASH>(g, t, st, ctl, blockIdx.x, k_begin, k_end);
+}
+
+// Many runs in one launch (continuous batching): block i executes task i --
+// a block of walkers of one request for that request's next steps.  The
+// request descriptors and the task table are read once per block.
+template <typename Real, int NS>
+__global__ void __launch_bounds__(kWalkBlock, (std::is_same<Real, float>::value && NS <= 2) ? 8 : 4)
+walk_batched_kernel(const ReqDesc<Real> *reqs, const BlockTask *tasks, int32_t n_tasks)
+{
+    if ((int32_t)blockIdx.x >= n_tasks) return;
+    __shared__ ReqDesc<Real> s_req;
+    __shared__ BlockTask s_task;
+    if (threadIdx.x == 0) {
+        s_task = tasks[blockIdx.x];
+        s_req = reqs[s_task.req];
+    }
+    __syncthreads();
+    walk_block<Real, NS, false>(s_req.g, s_req.t, s_req.st, s_req.ctl, s_task.block, s_task.k0, s_task.k1);
+}
+
+template <typename Real>
+cudaError_t launch_walk_batched(int ns_bucket, int32_t n_tasks, cudaStream_t stream, const ReqDesc<Real> *reqs,
+                                const BlockTask *tasks)
+{
+    if (n_tasks <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)n_tasks);
+    if (ns_bucket <= 1)
+        walk_batched_kernel<Real, 1><<<grid, kWalkBlock, 0, stream>>>(reqs, tasks, n_tasks);
+    else if (ns_bucket <= 2)
+        walk_batched_kernel<Real, 2><<<grid, kWalkBlock, 0, stream>>>(reqs, tasks, n_tasks);
+    else if (ns_bucket <= 4)
+        walk_batched_kernel<Real, 4><<<grid, kWalkBlock, 0, stream>>>(reqs, tasks, n_tasks);
+    else
+        walk_batched_kernel<Real, 8><<<grid, kWalkBlock, 0, stream>>>(reqs, tasks, n_tasks);
+    return cudaGetLastError();
 }
 
 // Host-side launcher, instantiated in walk_fp64.cu / walk_fp32.cu.
