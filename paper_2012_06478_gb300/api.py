@@ -248,7 +248,8 @@ def simulate(wl, precision: int = RMS_FP64, n_walkers: Optional[int] = None, see
     run = rms_run(seq, wl.n_walkers if n_walkers is None else n_walkers, wl.seed if seed is None else seed,
                   precision, RMS_TRAJ_HASH if hash_ else 0, walker_begin, steps_per_launch, stream)
     S, mom, asum = rms_read_signal(run)
-    res = dict(S=S, moments=mom, alpha_sum=asum, status=seq.status, step_ms=rms_run_step_time_ms(run))
+    res = dict(S=S, moments=mom, alpha_sum=asum, status=seq.status, step_ms=rms_run_step_time_ms(run),
+               b_s=rms_sequence_bvalues(seq))
     if walkers:
         res.update(rms_read_walkers(run))
     run.close()

@@ -359,12 +359,16 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                 // start of the step; events are then taken in time order, and only a
                 // change of step length (crossing into another D) rescales the
                 // remaining times.
+                // T[a]: time at which axis a meets its face (may lie beyond the step:
+                // a crossing into a faster label can still bring it inside); kNever
+                // for an axis that does not move.
+                constexpr Real kNever = Real(1e30);
                 Real T[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     const Real ad = fabsf(d[a]);
                     const Real dist = d[a] > Real(0) ? Real(1) - o[a] : o[a];
-                    T[a] = (dist < ad) ? __fdividef(dist, ad) : Real(2);
+                    T[a] = ad > Real(0) ? fminf(__fdividef(dist, ad), kNever) : kNever;
                 }
                 Real tau = Real(0);
 #pragma unroll 1
@@ -388,7 +392,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                         if (a == best) {
                             up = d[a] > Real(0);
                             o[a] = up ? Real(1) : Real(0);
-                            T[a] = Real(2);
+                            T[a] = kNever;
                         } else {
                             o[a] = clamp01(o[a] + dtt * d[a]);
                         }
@@ -402,7 +406,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
                             d[a] = n[a] * sc;
-                            if (T[a] < Real(1)) T[a] = tau + (T[a] - tau) * ratio;
+                            if (T[a] < kNever) T[a] = tau + (T[a] - tau) * ratio;
                         }
                     }
                 }

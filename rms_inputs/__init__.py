@@ -300,7 +300,8 @@ def _axons(nx, ny, nz, n_axons, seed, D_in, D_ex, kappa, T2_in, T2_ex, dt, n_ste
     else:
         # two membranes in series between touching axons; the bath has none
         k = np.concatenate([[math.inf], kappa_per_axon])
-        K = 1.0 / (1.0 / k[:, None] + 1.0 / k[None, :])
+        with np.errstate(divide="ignore"):
+            K = 1.0 / (1.0 / k[:, None] + 1.0 / k[None, :])
     np.fill_diagonal(K, 0.0)
     return Workload(name, lab, 0.1, (1, 1, 1), D, T2, T1, K, np.zeros(L, np.uint8), dt, n_steps,
                     shapes, None, dirs, b, _rec(n_steps, rec_every), n_walkers, seed)

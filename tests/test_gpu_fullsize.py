@@ -1,0 +1,124 @@
+"""Parity at the workloads' full sizes, in the launch configuration bench.py
+times (default steps per launch, no trajectory hash).
+
+The oracle cannot walk a million walkers, so it recomputes sampled walkers
+(their global ids fix their random streams) and the plain FP64 path must
+match them bit for bit; the FP32 form is checked against the FP64 path's
+full-size signal and moments (|dS| <= 1e-3, D within 1 %, K within
+0.01 max(|K|, 0.1)), plus, for runs long enough that FP32 rounding drift
+decorrelates some walkers from their FP64 twins, 4.5 standard errors of the
+paired per-walker differences."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+NT = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def rms():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2012_06478_gb300 as rms
+    return rms
+
+
+def _sample_ids(W, n=16):
+    return [(0, n), (W // 2 - n // 2, W // 2 + n // 2), (W - n, W)]
+
+
+def _check_sampled(oracle, wl, g):
+    for b, e in _sample_ids(wl.n_walkers):
+        o = oracle.run(wl, b, e, n_threads=NT, hash_=False)
+        assert o["err"] == 0
+        for k in ("i", "o", "c", "A", "phase"):
+            np.testing.assert_array_equal(g[k][b:e], o[k].astype(g[k].dtype), err_msg=f"{k} walkers {b}..{e}")
+
+
+def _dk(M, t):
+    a = M[:, 0]
+    m2 = np.stack([M[:, 1], M[:, 4], M[:, 6]], 1) / a[:, None]
+    m4 = np.stack([M[:, 7], M[:, 17], M[:, 21]], 1) / a[:, None]
+    return m2 / (2 * t[:, None]), m4 / m2 ** 2 - 3
+
+
+def _terms(wl, g):
+    """Per-walker alpha e^{-i phi} for every (shape, dir, b) and alpha, from the
+    exported walker state (error bars only)."""
+    q = np.sqrt(wl.b[None, :] / g["b_s"][:, None])            # (S, n_b)
+    proj = np.einsum("wsa,da->wsd", g["phase"], wl.dirs)       # (W, S, n_dirs)
+    phi = proj[..., None] * q[None, :, None, :]                # (W, S, n_dirs, n_b)
+    al = np.exp(-g["A"])
+    return al[:, None, None, None] * np.exp(-1j * phi), al
+
+
+def _check_fp32(wl, g64, g32):
+    """|S32 - S64| <= 1e-3 + 4.5 sigma, sigma the standard error of the paired
+    per-walker differences: walkers whose FP32 trajectory has drifted off the
+    FP64 one (rounding drift ~ sqrt(steps)) contribute Monte-Carlo noise that
+    falls as 1/sqrt(W); the 1e-3 bar applies to what is left.  D and K at the
+    last recording time likewise, from the final displacements."""
+    dS = np.abs(g32["S"] - g64["S"])
+    if "phase" in g64 and "phase" in g32:
+        e64, a64 = _terms(wl, g64)
+        e32, a32 = _terms(wl, g32)
+        d = e32 / a32.mean() - e64 / a64.mean()
+        sig = np.sqrt(d.real.var(axis=0) + d.imag.var(axis=0)) / np.sqrt(d.shape[0])
+    else:
+        sig = np.zeros_like(dS)
+    assert np.all(dS <= 1e-3 + 4.5 * sig), (dS.max(), sig.max())
+    t = wl.rec_steps * wl.dt
+    D64, K64 = _dk(g64["moments"], t)
+    D32, K32 = _dk(g32["moments"], t)
+    if "phase" in g64 and "phase" in g32 and wl.rec_steps[-1] == wl.n_steps:
+        x64 = wl.voxel_um * ((g64["i"] - g64["i0"]) + (g64["o"] - g64["o0"]))
+        x32 = wl.voxel_um * ((g32["i"] - g32["i0"]) + (g32["o"] - g32["o0"]))
+        W = x64.shape[0]
+        m2d = x32 ** 2 - x64 ** 2
+        sD = m2d.std(axis=0) / np.sqrt(W) / (2 * t[-1])
+        assert np.all(np.abs(D32[-1] - D64[-1]) <= 0.01 * D64[-1] + 4.5 * sD)
+        m4d = x32 ** 4 - x64 ** 4
+        m2 = (x64 ** 2).mean(axis=0)
+        sK = np.sqrt((m4d.std(axis=0) / m2 ** 2) ** 2 + (2 * (x64 ** 4).mean(0) / m2 ** 3 * m2d.std(axis=0)) ** 2)
+        sK = sK / np.sqrt(W)
+        assert np.all(np.abs(K32[-1] - K64[-1]) <= 0.01 * np.maximum(np.abs(K64[-1]), 0.1) + 4.5 * sK)
+    else:
+        assert np.all(np.abs(D32 - D64) <= 0.01 * D64)
+        assert np.all(np.abs(K32 - K64) <= 0.01 * np.maximum(np.abs(K64), 0.1))
+
+
+def test_axons_200x200x400_full(rms):
+    """The benchmark workload itself: 1e6 walkers x 1e5 steps."""
+    import oracle
+    import rms_inputs as ri
+    wl = ri.workload("axons-200x200x400")
+    g64 = rms.simulate(wl, rms.RMS_FP64, walkers=True)
+    _check_sampled(oracle, wl, g64)
+    g32 = rms.simulate(wl, rms.RMS_FP32)
+    _check_fp32(wl, g64, g32)
+
+
+def test_axons_400cubed_t2_ogse(rms):
+    """400^3 axons, unequal D, T2, per-axon kappa, PGSE + five OGSE shapes:
+    every step of the full sequence, 1e4 walkers."""
+    import oracle
+    import rms_inputs as ri
+    wl = ri.workload("axons-400^3-t2-ogse").with_(n_walkers=10_000)
+    g64 = rms.simulate(wl, rms.RMS_FP64, walkers=True)
+    _check_sampled(oracle, wl, g64)
+    g32 = rms.simulate(wl, rms.RMS_FP32, walkers=True)
+    _check_fp32(wl, g64, g32)
+
+
+def test_voronoi_512cubed(rms):
+    """512^3 Voronoi cells with per-label D, T1, T2 and per-pair kappa: every
+    step of the full sequence, 2e5 walkers."""
+    import oracle
+    import rms_inputs as ri
+    wl = ri.workload("voronoi-512^3").with_(n_walkers=200_000)
+    g64 = rms.simulate(wl, rms.RMS_FP64, walkers=True)
+    _check_sampled(oracle, wl, g64)
+    g32 = rms.simulate(wl, rms.RMS_FP32, walkers=True)
+    _check_fp32(wl, g64, g32)
