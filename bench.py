@@ -169,6 +169,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def ncu_case(args):
+    """The small case the kernel profiles in profiles/ are captured on: the
+    workload's first `--ncu-case` steps, all walkers, one walk launch per form."""
+    import torch
+    import paper_2012_06478_gb300 as rms
+    wl = workload_of(args.workload)
+    n = args.ncu_case
+    wl = wl.with_(n_steps=n, G=np.asarray(wl.G)[:, :n], rec_steps=wl.rec_steps[wl.rec_steps <= n])
+    for prec in (rms.RMS_FP32, rms.RMS_FP64):
+        r = rms.simulate(wl, prec, steps_per_launch=n)
+        print(f"precision {prec}: {wl.n_walkers} walkers x {n} steps, walk {r['step_ms']:.2f} ms", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -179,10 +192,18 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64 plain-form steps")
     ap.add_argument("--fp64-warmup", type=int, default=1, help="untimed FP64 plain-form steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=512)
+    ap.add_argument("--serving-fp64", action="store_true", help="also serve the stream in the FP64 plain form")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ncu-case", type=int, default=0,
+                    help="profiling case: one FP32 and one FP64 run of the workload with this many steps "
+                         "(one walk launch each), no timing output")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.ncu_case:
+        return ncu_case(args)
 
     import torch
     import torch.distributed as dist
@@ -265,6 +286,9 @@ def main():
     pk = peaks()
     hbm = pk.get("hbm_gbs")
     achieved = alg_bytes / (walk_launch_ms * 1e-3) / 1e9
+    sm_mhz = (clk.summary().get("sm_mhz") or pk.get("sm_max_mhz") or 2070.0)
+    lane_peak = ISSUE_LANES_PER_CLOCK * sm_mhz * 1e6
+    lane_rate = INST_PER_WALKER_STEP_FP32 * (W * spl) / (walk_launch_ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t32 / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -279,14 +303,23 @@ def main():
         "max_abs_dS_fp32_vs_fp64": dS,
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if hbm else None, "traffic": None,
+                     "frac": (achieved / hbm) if hbm else None, "traffic": TRAFFIC_PER_LAUNCH,
                      "kernel": "walk_kernel<float,1,false>", "alg_bytes_per_walker_step": 2.0 * eps,
                      "walker_steps_per_launch": W * spl, "launch_ms": walk_launch_ms,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+                     "what": "label-lookup bytes (2 B per face event) against HBM copy bandwidth (of measured)"},
+        "roofline_binding": {"bound": "alu", "achieved": lane_rate, "peak": lane_peak, "unit": "lane-instr/s",
+                             "frac": lane_rate / lane_peak, "inst_per_walker_step": INST_PER_WALKER_STEP_FP32,
+                             "what": "issue slots: 152 SMs x 4 schedulers x 32 lanes x measured SM clock; work = "
+                                     "thread-instructions per walker-step (ncu) x walker-steps/s of the walk launches"},
         "clocks": clk.summary(),
     }
     if not args.no_e2e:
         line["e2e"] = e2e(rms, torch, wl, W, w_begin, sp, args, world, max_over_ranks)
+    if not args.no_serving and world == 1:
+        import rms_inputs as ri
+        line["serving"] = serving(rms, ri, value, args.serving_requests, rms.RMS_FP32, sp)
+        if args.serving_fp64:
+            line["serving_fp64"] = serving(rms, ri, value64, args.serving_requests, rms.RMS_FP64, sp)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     seq.close()
@@ -295,6 +328,83 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# Thread-instructions one walker-step of the FP32 walk kernel executes on the
+# axon workload (ncu: smsp__inst_executed x thread_inst_executed_per_inst_executed
+# / walker-steps; profiles/walk_kernel_fp32_axons-200x200x400.md).
+INST_PER_WALKER_STEP_FP32 = 367.0
+# DRAM bytes (read + write) of one walk launch of the benchmark workload (2000
+# steps x 1e6 walkers), from the same profile; None until measured.
+TRAFFIC_PER_LAUNCH = None
+ISSUE_LANES_PER_CLOCK = 152 * 4 * 32  # SMs x schedulers x lanes
+
+
+def serving_pool(ri):
+    """Resident substrates of the serving stream: each generator kind at
+    32^3, 64^3, 128^3, 256^3 (0.1 um voxels, D = 2, kappa = 0.01)."""
+    pool = {}
+    for n in (32, 64, 128, 256):
+        pool[("cylinder", n)] = ri.cylinder_labels(n, n / 3.2)
+        pool[("axons", n)] = ri.axon_labels(n, n, n, 0.1, max(2, int(round(200 * (n / 200.0) ** 2))), seed=40 + n)
+        pool[("voronoi", n)] = ri.voronoi_labels(n, max(8, int(1000 * (n / 512.0) ** 3)), seed=50 + n)
+    return pool
+
+
+def serving(rms, ri, capacity, n_requests, precision, sp):
+    """A seeded stream of requests with Poisson arrivals at 80% of the
+    measured capacity through the continuous-batching server; p50/p99 of
+    submit-to-result latency."""
+    import threading
+    reqs = ri.serving_requests(n_requests, seed=4)
+    pool = serving_pool(ri)
+    dt = 2e-4
+    subs, seqs = {}, []
+    for key, lab in pool.items():
+        L = int(lab.max()) + 1
+        K = np.full((L, L), 0.01)
+        np.fill_diagonal(K, 0.0)
+        subs[key] = rms.rms_create_substrate(lab, 0.1, np.full(L, 2.0), kappa=K, stream=sp)
+    for r in reqs:
+        n = r["n_steps"]
+        G = ri.pgse(0.25 * n * dt, 0.5 * n * dt, dt, n)[None, :]
+        rec = np.unique(np.linspace(n / 10, n, 10).astype(np.int64))
+        seqs.append(rms.rms_set_sequence(subs[(r["kind"], r["n"])], dt, G, ri.fibonacci_dirs(r["n_dirs"]),
+                                         np.array([0.0, 1.0, 2.0]), rec))
+    work = np.array([r["n_walkers"] * r["n_steps"] for r in reqs], dtype=np.float64)
+    rate = 0.8 * capacity / work.mean()
+    rng = np.random.default_rng(4)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+    srv = rms.Server(memory_budget_bytes=16 << 30, max_active=64, steps_per_tick=256)
+    tickets = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for k, r in enumerate(reqs):
+            delay = arrivals[k] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[k] = srv.submit(seqs[k], r["n_walkers"], r["seed"] % (2 ** 63), precision)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    for t in tickets:
+        srv.wait(t)
+    el = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    for q in seqs:
+        q.close()
+    for sb in subs.values():
+        sb.close()
+    return {"requests": len(reqs), "precision": "fp32" if precision == rms.RMS_FP32 else "fp64",
+            "offered_load": 0.8, "arrival_rate_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "mean_ms": st["mean_ms"], "walker_steps_per_s": st["walker_steps_per_s"], "wall_s": el,
+            "peak_in_flight": st["peak_in_flight"], "ticks": st["ticks"], "graph_updates": st["graph_updates"],
+            "graph_instantiations": st["graph_instantiations"],
+            "stream": "requests from 12 resident substrates (cylinder/axons/voronoi at 32^3..256^3), "
+                      "walkers 1e4-1e6 and steps 1e3-5e4 log-uniform, 6-64 directions"}
 
 
 def e2e(rms, torch, wl, W, w_begin, sp, args, world, max_over_ranks):
