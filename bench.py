@@ -333,10 +333,10 @@ def main():
 # Thread-instructions one walker-step of the FP32 walk kernel executes on the
 # axon workload (ncu: smsp__inst_executed x thread_inst_executed_per_inst_executed
 # / walker-steps; profiles/walk_kernel_fp32_axons-200x200x400.md).
-INST_PER_WALKER_STEP_FP32 = 367.0
+INST_PER_WALKER_STEP_FP32 = 355.1
 # DRAM bytes (read + write) of one walk launch of the benchmark workload (2000
 # steps x 1e6 walkers), from the same profile; None until measured.
-TRAFFIC_PER_LAUNCH = None
+TRAFFIC_PER_LAUNCH = 153.1e6
 ISSUE_LANES_PER_CLOCK = 152 * 4 * 32  # SMs x schedulers x lanes
 
 
