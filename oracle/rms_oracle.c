@@ -48,7 +48,6 @@
 #define TAG_PERM 3u
 
 /* error bits reported through rmso_run's return value */
-#define RMSO_ERR_FOURTH_EVENT 1
 #define RMSO_ERR_BAD_ARG 4
 #define RMSO_ERR_OOM 8
 
@@ -381,76 +380,69 @@ static double clamp01(double x)
 
 /* One step's face walk (Sec. 2.2 items 3-4, Sec. 2.1.3, Fig. 2).
  *
- * Time within the step is the fraction f in (0,1]; in the walker's current
- * label c the displacement per unit fraction is d = n s_c (voxel units).
- * Repeat:
- *   for each axis a with d_a != 0, the distance to the face ahead is
- *   dist_a = 1 - o_a (d_a > 0) or o_a (d_a < 0); that face is reached in
- *   this step iff dist_a < f |d_a|, at fraction t_a = dist_a / |d_a|.
- *   No face reached: o += f d, done.  Otherwise take the smallest t_a
- *   (ties: lowest axis, x < y < z), t* = min(t_a, f); move the other axes
- *   by t* d, put o_a exactly on the face, f -= t*.  The voxel across the face
+ * Time within the step runs over [0, 1]; in the walker's current label c the
+ * displacement per unit time is d = n s_c (voxel units).  For each axis a
+ * with d_a != 0 the face ahead is dist_a = 1 - o_a (d_a > 0) or o_a (d_a < 0)
+ * away and is met at time T_a = dist_a / |d_a| (from the step start; it may
+ * lie beyond the step).  Events are taken in time order (smallest T first,
+ * ties to the lowest axis, x < y < z) while T < 1:
+ *   the other axes move to that time (o += (T - tau) d, clamped to [0,1]),
+ *   the event axis is put exactly on its face, and the voxel across the face
  *   has label c' (periodic lookups i mod N; beyond a non-periodic edge there
  *   is an impermeable wall):
  *     c' == c                       -> cross (transparent face, Sec. 2.2 item 3)
- *     word[e] < T[c][c'] (Eq. 3)    -> cross into c'; the remaining fraction f
- *                                      is kept and the step length becomes s_c'
+ *     word[e] < T[c][c'] (Eq. 3)    -> cross into c' (the remaining time of the
+ *                                      step is kept; the step length becomes s_c')
  *     otherwise                     -> reflect: n_a = -n_a (elastic collision)
- *   where e is the index of this event in the step and word[0], word[1]
- *   are words 2, 3 of the step's DIR call, word[2] word 0 of its PERM call.  With s_c < 1 for every label each axis meets at most one face
- *   per step (the corner reflector), so a fourth event is an error.
- * Every coordinate is clamped to [0,1] after each move.  The relaxation
- * exponent accumulates (segment fraction) x (dt / T of the segment's label). */
+ *   where e is the index of this event in the step and word[0], word[1] are
+ *   words 2, 3 of the step's DIR call, word[2] word 0 of its PERM call.
+ * An axis meets at most one face per step (with s_c < 1 a crossed or
+ * reflected axis would need a whole voxel to meet another: the corner
+ * reflector), so its time is then set to infinity.  A crossing into a label
+ * with another step length changes the speed: the remaining axes' times are
+ * then recomputed from their current positions, T_a = tau + dist_a / |d_a|.
+ * Finally every axis moves by (1 - tau) d and is clamped to [0,1].  The
+ * relaxation exponent accumulates (segment duration) x (dt / T of the
+ * segment's label). */
 static int walk_step(const ctx *X, uint64_t w, uint32_t k, walker *s, double n[3],
                      const uint32_t perm01[2], const uint32_t *perm2_given, int mode)
 {
     const rmso_config *cfg = X->cfg;
     const int L = cfg->n_labels;
     const int32_t N[3] = {cfg->nx, cfg->ny, cfg->nz};
-    double f = 1.0;
     double sc = X->s[s->c];
     double rate = X->dtR[mode][s->c];
-    for (int ev = 0;; ev++) {
-        double d[3] = {n[0] * sc, n[1] * sc, n[2] * sc};
-        int best = -1;
-        double tbest = 0.0;
-        for (int a = 0; a < 3; a++) {
-            double dist, ad;
-            if (d[a] > 0.0) {
-                dist = 1.0 - s->o[a];
-                ad = d[a];
-            } else if (d[a] < 0.0) {
-                dist = s->o[a];
-                ad = -d[a];
-            } else {
-                continue;
-            }
-            if (dist < f * ad) {
-                double t = dist / ad;
-                if (best < 0 || t < tbest) {
-                    best = a;
-                    tbest = t;
-                }
-            }
+    double d[3] = {n[0] * sc, n[1] * sc, n[2] * sc};
+    double T[3];
+    for (int a = 0; a < 3; a++) {
+        if (d[a] > 0.0)
+            T[a] = (1.0 - s->o[a]) / d[a];
+        else if (d[a] < 0.0)
+            T[a] = s->o[a] / (-d[a]);
+        else
+            T[a] = INFINITY;
+    }
+    double tau = 0.0;
+    for (int ev = 0; ev < 3; ev++) {
+        int best = 0;
+        double tmin = T[0];
+        if (T[1] < tmin) {
+            best = 1;
+            tmin = T[1];
         }
-        if (best < 0) {
-            for (int a = 0; a < 3; a++) s->o[a] = clamp01(s->o[a] + f * d[a]);
-            s->A = s->A + f * rate;
-            return 0;
+        if (T[2] < tmin) {
+            best = 2;
+            tmin = T[2];
         }
-        if (ev == 3) {
-            /* cannot happen when every s_c < 1; report and finish the step */
-            for (int a = 0; a < 3; a++) s->o[a] = clamp01(s->o[a] + f * d[a]);
-            s->A = s->A + f * rate;
-            return RMSO_ERR_FOURTH_EVENT;
-        }
-        double t = tbest < f ? tbest : f;
+        if (!(tmin < 1.0)) break;
+        const double dt_seg = tmin - tau;
         for (int a = 0; a < 3; a++)
-            if (a != best) s->o[a] = clamp01(s->o[a] + t * d[a]);
-        int up = d[best] > 0.0;
+            if (a != best) s->o[a] = clamp01(s->o[a] + dt_seg * d[a]);
+        const int up = d[best] > 0.0;
         s->o[best] = up ? 1.0 : 0.0;
-        s->A = s->A + t * rate;
-        f = f - t;
+        s->A = s->A + dt_seg * rate;
+        tau = tmin;
+        T[best] = INFINITY;
         s->n_events++;
 
         int64_t j = s->i[best] + (up ? 1 : -1);
@@ -468,8 +460,8 @@ static int walk_step(const ctx *X, uint64_t w, uint32_t k, walker *s, double n[3
         } else if (c2 < 0) {
             cross = 0;
         } else {
-            uint32_t T = X->T[(size_t)s->c * L + c2];
-            if (T == 0u) {
+            uint32_t Th = X->T[(size_t)s->c * L + c2];
+            if (Th == 0u) {
                 cross = 0;
             } else {
                 uint32_t word;
@@ -482,7 +474,7 @@ static int walk_step(const ctx *X, uint64_t w, uint32_t k, walker *s, double n[3
                     draw(cfg->seed, w, k, TAG_PERM, 0u, p4);
                     word = p4[0];
                 }
-                cross = word < T;
+                cross = word < Th;
             }
         }
         if (cross) {
@@ -490,15 +482,30 @@ static int walk_step(const ctx *X, uint64_t w, uint32_t k, walker *s, double n[3
             s->o[best] = up ? 0.0 : 1.0;
             if (c2 != s->c) {
                 s->c = c2;
-                sc = X->s[c2];
-                rate = X->dtR[mode][c2];
                 s->n_cross++;
+                rate = X->dtR[mode][c2];
+                if (X->s[c2] != sc) {
+                    sc = X->s[c2];
+                    for (int a = 0; a < 3; a++) {
+                        d[a] = n[a] * sc;
+                        if (T[a] == INFINITY) continue;
+                        if (d[a] > 0.0)
+                            T[a] = tau + (1.0 - s->o[a]) / d[a];
+                        else
+                            T[a] = tau + s->o[a] / (-d[a]);
+                    }
+                }
             }
         } else {
             n[best] = -n[best];
+            d[best] = -d[best];
             s->n_refl++;
         }
     }
+    const double rem = 1.0 - tau;
+    for (int a = 0; a < 3; a++) s->o[a] = clamp01(s->o[a] + rem * d[a]);
+    s->A = s->A + rem * rate;
+    return 0;
 }
 
 /* Sec. 2.3, Eq. 7 discretised: phi = sum_k (dt G_k) . x_k with x_k the

@@ -896,8 +896,6 @@ static rms_status finish(rms_run_handle *r)
     if (*(volatile int32_t *)r->h_cancel) return fail(RMS_E_CANCELLED, "run was cancelled");
     int32_t status = 0;
     RMS_CUDA(cudaMemcpy(&status, r->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
-    if (status & kErrFourthEvent)
-        return fail(RMS_E_DEVICE, "a step met a fourth face (some step length >= voxel size)");
     if (status) return fail(RMS_E_DEVICE, "device status " + std::to_string(status));
     return RMS_OK;
 }

@@ -56,7 +56,7 @@ constexpr int kMoments = 22;  // alpha, 6 second-order, 15 fourth-order terms
 constexpr int kMaxShapes = 8;
 
 // Device error bits (status word).
-enum : int { kErrFourthEvent = 1, kErrTimeout = 4 };
+enum : int { kErrTimeout = 4 };
 
 // Walker state, structure of arrays, one entry per walker.
 template <typename Real>

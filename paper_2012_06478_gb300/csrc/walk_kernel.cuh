@@ -30,6 +30,29 @@ __device__ __forceinline__ Real clamp01(Real x)
     return x;
 }
 
+// FP64 comparisons on the integer ALU.  GB300's FP64 pipe is the scarce
+// resource of the plain form, and every comparison or clamp of a double
+// would occupy it.  The signed 64-bit pattern of a double orders exactly like
+// its value among the non-negative doubles, and its sign bit tells x > 0 and
+// x < 0 apart from +-0; the walk's positions, times and step vectors are
+// never NaN, so these give the same booleans as the IEEE comparisons.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool dgt0(double x) { return dbits(x) > 0; }  // x > 0
+__device__ __forceinline__ bool dlt0(double x)                           // x < 0
+{
+    const long long b = dbits(x);
+    return b < 0 && b != (long long)0x8000000000000000ULL;
+}
+// a < b for a, b >= +0 (no -0 and no NaN among the arguments)
+__device__ __forceinline__ bool dlt_nn(double a, double b) { return dbits(a) < dbits(b); }
+// if (x < 0) 0; else if (x > 1) 1; else x -- as clamp01, for any non-NaN x
+__device__ __forceinline__ double dclamp01(double x)
+{
+    const long long b = dbits(x);
+    if (b < 0) return b == (long long)0x8000000000000000ULL ? x : 0.0;
+    return b > 0x3FF0000000000000LL ? 1.0 : x;
+}
+
 // Sec. 2.2 item 2, the direction.  z = 1 - 2u is uniform on [-1, 1] for a
 // uniform point of the sphere (Archimedes); the azimuth is
 // phi = 2 pi (x1 + 1/2) 2^-32.  Its sine and cosine come from Taylor
@@ -48,12 +71,15 @@ __device__ __forceinline__ void octant_map(uint32_t oct, double cs, double sn, d
 
 __device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, double n[3])
 {
-    const double z = 1.0 - 2.0 * u01(x0);
+    // z = 1 - 2 u(x0) = (2^32 - 1 - 2 x0) 2^-32 and (m + 1/2) 2^-29 = (2 m + 1) 2^-30:
+    // exact integers scaled by powers of two, the same bits as the reference's
+    // step-by-step evaluation with fewer FP64 operations.
+    const double z = (double)(0xFFFFFFFFLL - 2LL * (long long)x0) * 0x1p-32;
     const double r = sqrt((1.0 - z) * (1.0 + z));
     const uint32_t oct = x1 >> 29;
     uint32_t m = x1 & 0x1FFFFFFFu;
     if (oct & 1u) m = 0x1FFFFFFFu - m;
-    const double th = (((double)m + 0.5) * 0x1p-29) * 0.78539816339744830962;
+    const double th = ((double)(2u * m + 1u) * 0x1p-30) * 0.78539816339744830962;
     const double t = th * th;
     double ps = 1.0 / 355687428096000.0;
     ps = -1.0 / 1307674368000.0 + t * ps;
@@ -297,71 +323,72 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                 }
                 return false;
             };
+            // Face times from the step start: axis a meets its face at T[a] = dist/|d_a|
+            // (beyond the step when >= 1); events are taken in time order (ties to the
+            // lower axis), an axis meets at most one face per step (s_c < 1: the corner
+            // reflector), and a crossing into a label of another step length
+            // recomputes the remaining times from the current positions.
             if constexpr (kF64) {
-                // Plain form: the reference's formulation, operation for operation.
-                // Remaining fraction f; candidates dist_a < f |d_a| at t_a = dist_a/|d_a|.
-                Real f = Real(1);
-                for (int ev = 0;; ++ev) {
-                    int best = -1;
-                    Real tbest = Real(0);
+                // Plain form: the reference's operation order; comparisons on the
+                // integer ALU (dgt0/dlt_nn/dclamp01 give the IEEE results).
+                const double kInf = __longlong_as_double(0x7FF0000000000000LL);
+                double T[3];
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        Real dist, ad;
-                        bool cand = true;
-                        if (d[a] > Real(0)) {
-                            dist = Real(1) - o[a];
-                            ad = d[a];
-                        } else if (d[a] < Real(0)) {
-                            dist = o[a];
-                            ad = -d[a];
-                        } else {
-                            cand = false;
-                            dist = ad = Real(1);
-                        }
-                        if (cand && dist < f * ad) {
-                            const Real tt = dist / ad;
-                            if (best < 0 || tt < tbest) {
-                                best = a;
-                                tbest = tt;
-                            }
-                        }
+                for (int a = 0; a < 3; ++a) {
+                    if (dgt0(d[a]))
+                        T[a] = (1.0 - o[a]) / d[a];
+                    else if (dlt0(d[a]))
+                        T[a] = o[a] / (-d[a]);
+                    else
+                        T[a] = kInf;
+                }
+                double tau = 0.0;
+#pragma unroll 1
+                for (int ev = 0; ev < 3; ++ev) {
+                    int best = 0;
+                    double tmin = T[0];
+                    if (dlt_nn(T[1], tmin)) {
+                        best = 1;
+                        tmin = T[1];
                     }
-                    if (best < 0 || ev == 3) {
-                        if (best >= 0) atomicOr(ctl.status, kErrFourthEvent);
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) o[a] = clamp01(o[a] + f * d[a]);
-                        if (t.any_relax) A = A + f * rate;
-                        break;
+                    if (dlt_nn(T[2], tmin)) {
+                        best = 2;
+                        tmin = T[2];
                     }
-                    const Real tt = tbest < f ? tbest : f;
+                    if (!dlt_nn(tmin, 1.0)) break;
+                    const double dts = tmin - tau;
                     bool up = false;
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         if (a == best) {
-                            up = d[a] > Real(0);
-                            o[a] = up ? Real(1) : Real(0);
+                            up = dgt0(d[a]);
+                            o[a] = up ? 1.0 : 0.0;
+                            T[a] = kInf;
                         } else {
-                            o[a] = clamp01(o[a] + tt * d[a]);
+                            o[a] = dclamp01(o[a] + dts * d[a]);
                         }
                     }
-                    if (t.any_relax) A = A + tt * rate;
-                    f = f - tt;
+                    if (t.any_relax) A = A + dts * rate;
+                    tau = tmin;
                     if (face(best, up, ev)) {
-                        sc = __ldg(t.s + c);
+                        const double sn = __ldg(t.s + c);
+                        if (dbits(sn) != dbits(sc)) {
+                            sc = sn;
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) d[a] = n[a] * sc;
+                            for (int a = 0; a < 3; ++a) {
+                                d[a] = n[a] * sc;
+                                if (dbits(T[a]) == 0x7FF0000000000000LL) continue;
+                                T[a] = dgt0(d[a]) ? tau + (1.0 - o[a]) / d[a] : tau + o[a] / (-d[a]);
+                            }
+                        }
                     }
                 }
+                const double rem = 1.0 - tau;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) o[a] = dclamp01(o[a] + rem * d[a]);
+                if (t.any_relax) A = A + rem * rate;
             } else {
-                // Precision form.  Each axis meets at most one face per step (s_c < 1:
-                // the corner reflector), and events on one axis leave the others'
-                // motion unchanged, so the three face times are found once, from the
-                // start of the step; events are then taken in time order, and only a
-                // change of step length (crossing into another D) rescales the
-                // remaining times.
-                // T[a]: time at which axis a meets its face (may lie beyond the step:
-                // a crossing into a faster label can still bring it inside); kNever
-                // for an axis that does not move.
+                // Precision form: the same walk in FP32 (approximate division).
                 constexpr Real kNever = Real(1e30);
                 Real T[3];
 #pragma unroll
@@ -401,12 +428,15 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                     tau = tmin;
                     if (face(best, up, ev)) {
                         const Real sn = __ldg(t.s + c);
-                        const Real ratio = __fdividef(sc, sn);
-                        sc = sn;
+                        if (sn != sc) {
+                            sc = sn;
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            d[a] = n[a] * sc;
-                            if (T[a] < kNever) T[a] = tau + (T[a] - tau) * ratio;
+                            for (int a = 0; a < 3; ++a) {
+                                d[a] = n[a] * sc;
+                                if (!(T[a] < kNever)) continue;
+                                const Real dist = d[a] > Real(0) ? Real(1) - o[a] : o[a];
+                                T[a] = tau + __fdividef(dist, fabsf(d[a]));
+                            }
                         }
                     }
                 }

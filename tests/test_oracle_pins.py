@@ -467,3 +467,28 @@ def test_direction_sampler_closed_form(oracle_lib):
         r = math.sqrt((1 - z) * (1 + z))  # 1 - z and 1 + z are exact
         np.testing.assert_allclose(n, [r * math.cos(phi), r * math.sin(phi), z], rtol=0, atol=1e-15)
         assert abs(np.dot(n, n) - 1.0) < 1e-15
+
+
+def test_speed_change_brings_a_face_inside_the_step(oracle_lib):
+    """Hand-derived step: from o = (0.95, 0.75, 0.5) with n = (0.6, 0.8, 0) in
+    a slow label (D = 0.5), the x face is crossed at t1 = 0.05 / (0.6 s0) into
+    a fast label (D = 3); at the old speed the y face (0.25 away) would lie
+    beyond the step (0.25 / (0.8 s0) > 1), at the new speed it is met at
+    t2 = t1 + (0.25 - 0.8 s0 t1) / (0.8 s1) < 1 and reflects (impermeable)."""
+    lab = np.array([[[0, 1], [2, 2]]])            # (z, y, x): (0,0)=0, (1,0)=1, y=1 row = 2
+    D = np.array([0.5, 3.0, 1.0])
+    K = np.zeros((3, 3))
+    K[0, 1] = 1e6                                 # 0 -> 1 always crosses, 1 -> 2 never
+    dt, l_p = 1e-3, 0.2
+    wl = make_workload(lab, voxel_um=l_p, D=D, kappa=K, dt=dt, n_steps=1, periodic=(1, 1, 0))
+    s0, s1 = ds_of(0.5, dt) / l_p, ds_of(3.0, dt) / l_p
+    t1 = 0.05 / (0.6 * s0)
+    assert 0.25 / (0.8 * s0) > 1.0
+    t2 = t1 + (0.25 - 0.8 * s0 * t1) / (0.8 * s1)
+    assert t2 < 1.0
+    i, o, c, A, n, counts, err = oracle_lib.walk_once(wl, [0, 0, 0], [0.95, 0.75, 0.5], 0, [0.6, 0.8, 0.0],
+                                                      perm=[0, 0, 0])
+    assert err == 0 and list(i) == [1, 0, 0] and c == 1
+    np.testing.assert_allclose(o, [(1 - t1) * 0.6 * s1, 1 - (1 - t2) * 0.8 * s1, 0.5], atol=1e-14)
+    np.testing.assert_array_equal(n, [0.6, -0.8, 0.0])
+    assert list(counts) == [2, 1, 1]
