@@ -309,22 +309,18 @@ static void init_walker(const ctx *X, uint64_t w, walker *s)
 /* Sec. 2.2 item 2, direction sampler (the paper does not name one):
  * Archimedes' hat-box theorem -- z = 1 - 2u is uniform on [-1,1] for a
  * uniform point of the sphere -- with the azimuth phi = 2 pi (x1 + 1/2) 2^-32
- * from the second word.  sin and cos of the azimuth come from Taylor
- * polynomials on [0, pi/4] (degree 17 / 16, truncation < 1e-18), after an
- * octant reduction done in integers, so only +, *, sqrt are used and the
- * result is the same bits on every IEEE machine.  One DIR call (k, call 0)
+ * from the second word.  sin and cos of the azimuth: an octant reduction in
+ * integers, then a table of 1024 angles of [0, pi/4] (itself from Taylor
+ * polynomials of degree 17 / 16), a 5th-order polynomial for the small
+ * offset from the nearest table angle and the angle-addition formula.  Only
+ * +, *, sqrt are used, so the result is the same bits on every IEEE machine.  One DIR call (k, call 0)
  * per step: words 0 and 1 give the direction, words 2 and 3 are the PERM
  * words of the step's first two membrane events. */
 static const double kPi4 = 0.78539816339744830962; /* pi/4 */
 
-static void direction_from(uint32_t x0, uint32_t x1, double n[3])
+/* sin and cos on [0, pi/4] by Taylor polynomials (degree 17 / 16). */
+static void poly_sincos(double th, double *sn, double *cs)
 {
-    const double z = 1.0 - 2.0 * u01(x0);
-    const double r = sqrt((1.0 - z) * (1.0 + z));
-    const uint32_t oct = x1 >> 29;
-    uint32_t m = x1 & 0x1FFFFFFFu;
-    if (oct & 1u) m = 0x1FFFFFFFu - m; /* odd octant: angle measured back from the octant's end */
-    const double th = (((double)m + 0.5) * 0x1p-29) * kPi4;
     const double t = th * th;
     double ps = 1.0 / 355687428096000.0;       /*  1/17! */
     ps = -1.0 / 1307674368000.0 + t * ps;       /* -1/15! */
@@ -334,7 +330,7 @@ static void direction_from(uint32_t x0, uint32_t x1, double n[3])
     ps = -1.0 / 5040.0 + t * ps;                /* -1/7!  */
     ps = 1.0 / 120.0 + t * ps;                  /*  1/5!  */
     ps = -1.0 / 6.0 + t * ps;                   /* -1/3!  */
-    const double sn = th + (th * t) * ps;
+    *sn = th + (th * t) * ps;
     double pc = 1.0 / 20922789888000.0;         /*  1/16! */
     pc = -1.0 / 87178291200.0 + t * pc;         /* -1/14! */
     pc = 1.0 / 479001600.0 + t * pc;            /*  1/12! */
@@ -343,8 +339,42 @@ static void direction_from(uint32_t x0, uint32_t x1, double n[3])
     pc = -1.0 / 720.0 + t * pc;                 /* -1/6!  */
     pc = 1.0 / 24.0 + t * pc;                   /*  1/4!  */
     pc = -1.0 / 2.0 + t * pc;                   /* -1/2!  */
-    const double cs = 1.0 + t * pc;
-    double cx, sy; /* cos and sin of oct pi/4 + th (even) or (oct+1) pi/4 - th (odd) */
+    *cs = 1.0 + t * pc;
+}
+
+/* The octant [0, pi/4] is cut into 1024 equal parts; TRIG[j] = (cos, sin) of
+ * the centre of part j, theta_j = (2j + 1) 2^-11 pi/4. */
+static double g_trig[1024][2];
+static pthread_once_t g_trig_once = PTHREAD_ONCE_INIT;
+
+static void build_trig(void)
+{
+    for (int j = 0; j < 1024; j++) {
+        const double th = ((double)(2 * j + 1) * 0x1p-11) * kPi4;
+        poly_sincos(th, &g_trig[j][1], &g_trig[j][0]);
+    }
+}
+
+static void direction_from(uint32_t x0, uint32_t x1, double n[3])
+{
+    pthread_once(&g_trig_once, build_trig);
+    const double z = 1.0 - 2.0 * u01(x0);
+    const double r = sqrt((1.0 - z) * (1.0 + z));
+    const uint32_t oct = x1 >> 29;
+    uint32_t m = x1 & 0x1FFFFFFFu;
+    if (oct & 1u) m = 0x1FFFFFFFu - m; /* odd octant: angle measured back from the octant's end */
+    /* angle (m + 1/2) 2^-29 pi/4 = theta_j + e: j = the top 10 bits of m, e the
+     * offset of the low 19 bits from the part's centre, |e| <= 2^-11 pi/4 */
+    const uint32_t j = m >> 19;
+    const int32_t lo = (int32_t)(m & 0x7FFFFu);
+    const double e = ((double)(2 * lo + 1 - (1 << 19)) * 0x1p-30) * kPi4;
+    const double t = e * e;
+    const double se = e + (e * t) * (-1.0 / 6.0 + t * (1.0 / 120.0)); /* truncation < 1e-25 */
+    const double ce = 1.0 + t * (-1.0 / 2.0 + t * (1.0 / 24.0));      /* truncation < 1e-22 */
+    const double cj = g_trig[j][0], sj = g_trig[j][1];
+    const double cs = cj * ce - sj * se; /* cos(theta_j + e) */
+    const double sn = sj * ce + cj * se; /* sin(theta_j + e) */
+    double cx, sy; /* cos and sin of oct pi/4 + angle (even) or (oct+1) pi/4 - angle (odd) */
     switch (oct) {
     case 0: cx = cs; sy = sn; break;
     case 1: cx = sn; sy = cs; break;

@@ -166,6 +166,19 @@ __global__ void pair_tables_kernel(int32_t L, const double *D, const double *kap
     T[idx] = thr;
 }
 
+// The azimuth table: (cos, sin) of the centres (2j + 1) 2^-11 pi/4 of the
+// 1024 parts of [0, pi/4].
+__global__ void trig_table_kernel(double *trig)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= kTrigParts) return;
+    const double th = ((double)(2 * j + 1) * 0x1p-11) * 0.78539816339744830962;
+    double sn, cs;
+    poly_sincos(th, sn, cs);
+    trig[2 * j] = cs;
+    trig[2 * j + 1] = sn;
+}
+
 // Per step: weights dt G_{s,k}, the step flags and the recording index.
 __global__ void step_tables_kernel(int64_t N, int32_t S, double dt, const double *G, const int64_t *rec,
                                    int32_t n_rec, double *wG64, float *wG32, uint8_t *flags, int32_t *rec_of)
@@ -526,7 +539,7 @@ extern "C" rms_status rms_destroy_substrate(rms_substrate *s)
 static void free_sequence(rms_sequence *q, cudaStream_t st)
 {
     void *p[] = {q->d_s64, q->d_dtR64, q->d_wG64, q->d_s32, q->d_dtR32, q->d_wG32, q->d_T, q->d_flags,
-                 q->d_mode, q->d_rec_of, q->d_dirs, q->d_b, q->d_bs, q->d_q};
+                 q->d_mode, q->d_rec_of, q->d_dirs, q->d_b, q->d_bs, q->d_q, q->d_trig};
     for (void *x : p)
         if (x) cudaFreeAsync(x, st);
 }
@@ -577,6 +590,8 @@ static rms_status set_sequence_impl(rms_substrate *sub, const rms_sequence_desc 
     RMS_TRY(upload(&q->d_dirs, d->dirs, (size_t)3 * d->n_dirs, st));
     RMS_TRY(upload(&q->d_b, d->b, (size_t)d->n_b, st));
     RMS_CUDA(cudaMallocAsync((void **)&q->d_bs, sizeof(double) * S, st));
+    RMS_CUDA(cudaMallocAsync((void **)&q->d_trig, sizeof(double) * 2 * kTrigParts, st));
+    trig_table_kernel<<<kTrigParts / 128, 128, 0, st>>>(q->d_trig);
     RMS_CUDA(cudaMallocAsync((void **)&q->d_q, sizeof(double) * S * d->n_b, st));
     double *d_G = nullptr;
     int64_t *d_rec = nullptr;
@@ -688,11 +703,11 @@ ReqDesc<Real> rms::run_desc(rms_run_handle *r)
                    sub->voxel_um};
     if constexpr (std::is_same<Real, float>::value) {
         d.t = Tables<float>{q->d_s32, q->d_dtR32, q->d_T, sub->L, q->d_wG32, q->d_flags, q->d_rec_of, q->d_mode,
-                            q->any_relax};
+                            q->any_relax, q->d_trig};
         d.st = r->st32;
     } else {
         d.t = Tables<double>{q->d_s64, q->d_dtR64, q->d_T, sub->L, q->d_wG64, q->d_flags, q->d_rec_of, q->d_mode,
-                             q->any_relax};
+                             q->any_relax, q->d_trig};
         d.st = r->st64;
     }
     d.ctl.seed = r->seed;

@@ -44,6 +44,33 @@ __device__ __forceinline__ U4 draw(uint64_t seed, uint64_t w, uint32_t step, uin
 // (x + 1/2) 2^-32: uniform in (0,1), exact in FP64.
 __device__ __forceinline__ double u01(uint32_t x) { return ((double)x + 0.5) * 0x1p-32; }
 
+// sin and cos on [0, pi/4] by Taylor polynomials (degree 17 / 16, truncation
+// below 1e-18), separate multiplies and adds.  Used to fill the azimuth table.
+__device__ __forceinline__ void poly_sincos(double th, double &sn, double &cs)
+{
+    const double t = th * th;
+    double ps = 1.0 / 355687428096000.0;
+    ps = -1.0 / 1307674368000.0 + t * ps;
+    ps = 1.0 / 6227020800.0 + t * ps;
+    ps = -1.0 / 39916800.0 + t * ps;
+    ps = 1.0 / 362880.0 + t * ps;
+    ps = -1.0 / 5040.0 + t * ps;
+    ps = 1.0 / 120.0 + t * ps;
+    ps = -1.0 / 6.0 + t * ps;
+    sn = th + (th * t) * ps;
+    double pc = 1.0 / 20922789888000.0;
+    pc = -1.0 / 87178291200.0 + t * pc;
+    pc = 1.0 / 479001600.0 + t * pc;
+    pc = -1.0 / 3628800.0 + t * pc;
+    pc = 1.0 / 40320.0 + t * pc;
+    pc = -1.0 / 720.0 + t * pc;
+    pc = 1.0 / 24.0 + t * pc;
+    pc = -1.0 / 2.0 + t * pc;
+    cs = 1.0 + t * pc;
+}
+
+constexpr int kTrigParts = 1024;  // parts of the octant [0, pi/4] in the azimuth table
+
 // SplitMix64 finaliser (Steele, Lea & Flood 2014), the trajectory checksum.
 __device__ __forceinline__ uint64_t mix64(uint64_t z)
 {
@@ -91,6 +118,7 @@ struct Tables {
     const int32_t *rec_of;  // [step]: recording index or -1
     const uint8_t *mode;    // [step] relaxation mode (or nullptr = 0)
     int32_t any_relax;
+    const double *trig;     // [part][cos, sin] of the azimuth table (FP64 form)
 };
 
 struct RunCtl {

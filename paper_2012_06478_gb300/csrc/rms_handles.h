@@ -40,6 +40,7 @@ struct rms_sequence {
     uint8_t *d_flags = nullptr, *d_mode = nullptr;
     int32_t *d_rec_of = nullptr;
     double *d_dirs = nullptr, *d_b = nullptr, *d_bs = nullptr, *d_q = nullptr;
+    double *d_trig = nullptr;  // azimuth table (FP64 form)
     std::atomic<int> refs{0};
 };
 

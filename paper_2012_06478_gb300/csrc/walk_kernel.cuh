@@ -56,9 +56,12 @@ __device__ __forceinline__ double dclamp01(double x)
 // Sec. 2.2 item 2, the direction.  z = 1 - 2u is uniform on [-1, 1] for a
 // uniform point of the sphere (Archimedes); the azimuth is
 // phi = 2 pi (x1 + 1/2) 2^-32.  Its sine and cosine come from Taylor
-// polynomials on [0, pi/4] after an octant reduction in integers, so the FP64
-// form uses only +, * and sqrt -- the same bits as any IEEE machine given the
-// same operation order -- and no warp ever loops on a rejection.
+// polynomials after an octant reduction in integers -- in the FP64 form a
+// table of 1024 angles of [0, pi/4] (filled by poly_sincos), a 5th-order
+// polynomial for the offset from the nearest table angle and the
+// angle-addition formula -- so the FP64 form uses only +, * and sqrt (the
+// same bits as any IEEE machine given the same operation order), and no
+// warp ever loops on a rejection.
 __device__ __forceinline__ void octant_map(uint32_t oct, double cs, double sn, double &cx, double &sy)
 {
     const bool swap = ((oct + 1u) >> 1) & 1u;  // octants 1, 2, 5, 6
@@ -69,36 +72,27 @@ __device__ __forceinline__ void octant_map(uint32_t oct, double cs, double sn, d
     sy = negy ? -b : b;
 }
 
-__device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, double n[3])
+__device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, const double *__restrict__ trig,
+                                               double n[3])
 {
-    // z = 1 - 2 u(x0) = (2^32 - 1 - 2 x0) 2^-32 and (m + 1/2) 2^-29 = (2 m + 1) 2^-30:
-    // exact integers scaled by powers of two, the same bits as the reference's
-    // step-by-step evaluation with fewer FP64 operations.
+    // z = 1 - 2 u(x0) = (2^32 - 1 - 2 x0) 2^-32: an exact integer scaled by a
+    // power of two, the same bits as the reference's step-by-step evaluation.
     const double z = (double)(0xFFFFFFFFLL - 2LL * (long long)x0) * 0x1p-32;
     const double r = sqrt((1.0 - z) * (1.0 + z));
     const uint32_t oct = x1 >> 29;
     uint32_t m = x1 & 0x1FFFFFFFu;
     if (oct & 1u) m = 0x1FFFFFFFu - m;
-    const double th = ((double)(2u * m + 1u) * 0x1p-30) * 0.78539816339744830962;
-    const double t = th * th;
-    double ps = 1.0 / 355687428096000.0;
-    ps = -1.0 / 1307674368000.0 + t * ps;
-    ps = 1.0 / 6227020800.0 + t * ps;
-    ps = -1.0 / 39916800.0 + t * ps;
-    ps = 1.0 / 362880.0 + t * ps;
-    ps = -1.0 / 5040.0 + t * ps;
-    ps = 1.0 / 120.0 + t * ps;
-    ps = -1.0 / 6.0 + t * ps;
-    const double sn = th + (th * t) * ps;
-    double pc = 1.0 / 20922789888000.0;
-    pc = -1.0 / 87178291200.0 + t * pc;
-    pc = 1.0 / 479001600.0 + t * pc;
-    pc = -1.0 / 3628800.0 + t * pc;
-    pc = 1.0 / 40320.0 + t * pc;
-    pc = -1.0 / 720.0 + t * pc;
-    pc = 1.0 / 24.0 + t * pc;
-    pc = -1.0 / 2.0 + t * pc;
-    const double cs = 1.0 + t * pc;
+    // angle (m + 1/2) 2^-29 pi/4 = theta_j + e, theta_j = (2j + 1) 2^-11 pi/4 the
+    // centre of part j = top 10 bits of m, |e| <= 2^-11 pi/4
+    const uint32_t j = m >> 19;
+    const int32_t lo = (int32_t)(m & 0x7FFFFu);
+    const double e = ((double)(2 * lo + 1 - (1 << 19)) * 0x1p-30) * 0.78539816339744830962;
+    const double t = e * e;
+    const double se = e + (e * t) * (-1.0 / 6.0 + t * (1.0 / 120.0));
+    const double ce = 1.0 + t * (-1.0 / 2.0 + t * (1.0 / 24.0));
+    const double cj = __ldg(trig + 2 * j), sj = __ldg(trig + 2 * j + 1);
+    const double cs = cj * ce - sj * se;
+    const double sn = sj * ce + cj * se;
     double cx, sy;
     octant_map(oct, cs, sn, cx, sy);
     n[0] = r * cx;
@@ -107,7 +101,7 @@ __device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, double 
 }
 
 // FP32 form of the same sampler (shorter polynomials: truncation below 1e-8).
-__device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, float n[3])
+__device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, const double *, float n[3])
 {
     const float z = -((float)(int32_t)(x0 ^ 0x80000000u) + 0.5f) * 0x1p-31f;
     const float r = sqrtf((1.0f - z) * (1.0f + z));
@@ -245,7 +239,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
             //      the Bernoulli words of the step's first two membrane events)
             const U4 x = draw(ctl.seed, w, (uint32_t)k, kTagDir, 0u);
             Real n[3];
-            direction_from(x.x, x.y, n);
+            direction_from(x.x, x.y, t.trig, n);
             // ---- face walk (Sec. 2.2 items 3-4)
             const int mode = t.mode ? (int)__ldg(t.mode + (k - 1)) : 0;
             Real sc = __ldg(t.s + c);
