@@ -256,7 +256,10 @@ def main():
     with Clocks(local) as clk:
         ms32, walk32, res32 = timed(rms.RMS_FP32, args.warmup, args.steps)
     # FP64 plain form, same workload
-    ms64, walk64, res64 = timed(rms.RMS_FP64, args.fp64_warmup, args.fp64_steps)
+    if args.fp64_steps > 0:
+        ms64, walk64, res64 = timed(rms.RMS_FP64, args.fp64_warmup, args.fp64_steps)
+    else:
+        ms64, walk64, res64 = [float("nan")], [], res32
 
     def max_over_ranks(x):
         if world == 1:
@@ -269,7 +272,7 @@ def main():
     t64 = max_over_ranks(sum(ms64))
     ws = W * wl.n_steps
     value = world * ws * args.steps / (t32 * 1e-3)
-    value64 = world * ws * args.fp64_steps / (t64 * 1e-3)
+    value64 = world * ws * args.fp64_steps / (t64 * 1e-3) if args.fp64_steps > 0 else None
     dS = float(np.abs(res32[0] - res64[0]).max())
     # FP32 form against the FP64 plain form on the same walkers: D and K along
     # x, y, z at every recording time (Sec. 2.3, narrow pulse)
@@ -312,7 +315,7 @@ def main():
                    "precision": "fp32 form (headline); fp64 plain form in fp64_plain",
                    "l2": "flushed between timed iterations (256 MiB write)", "parallelism": f"walker shards x{world}"},
         "fp64_plain": {"value": value64, "unit": UNIT, "dtype": "f64", "steps": args.fp64_steps, "warmup": args.fp64_warmup,
-                       "ms_per_step": t64 / args.fp64_steps},
+                       "ms_per_step": t64 / args.fp64_steps if args.fp64_steps > 0 else None},
         "fp32_vs_fp64": fp32_err,
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -331,7 +334,7 @@ def main():
     if not args.no_serving and world == 1:
         import rms_inputs as ri
         line["serving"] = serving(rms, ri, value, args.serving_requests, rms.RMS_FP32, sp)
-        if args.serving_fp64:
+        if args.serving_fp64 and value64:
             line["serving_fp64"] = serving(rms, ri, value64, args.serving_requests, rms.RMS_FP64, sp)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)

@@ -112,7 +112,7 @@ typedef struct {
                                  the average of g(t)/|g| over step k (row = shape) */
     const uint8_t *mode;      /* host, n_steps or NULL: relaxation during step k: 0 = T2, 1 = T1
                                  (stimulated-echo mixing time), 2 = none */
-    int32_t n_dirs;           /* >= 1 */
+    int32_t n_dirs;           /* >= 1; n_shapes * n_dirs * n_b <= 8e6 */
     const double *dirs;       /* host, n_dirs*3 unit gradient directions */
     int32_t n_b;              /* >= 1 */
     const double *b;          /* host, n_b b-values (ms/um^2), >= 0 */

@@ -302,7 +302,7 @@ readout_kernel(const Real *phase, const Real *phase_c, const Real *A, const Real
 {
     __shared__ double sP[kRoTile][kMaxShapes * 3];
     __shared__ double sAl[kRoTile];
-    const int combo = blockIdx.x * kRoBlock + threadIdx.x;
+    const int combo = blockIdx.y * kRoBlock + threadIdx.x;  // grid: x = walker chunk, y = combination group
     int s = 0;
     double qq = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
     if (combo < n_combo) {
@@ -314,7 +314,7 @@ readout_kernel(const Real *phase, const Real *phase_c, const Real *A, const Real
         g1 = dirs[3 * gi + 1];
         g2 = dirs[3 * gi + 2];
     }
-    const int64_t w0 = (int64_t)blockIdx.y * kRoChunk;
+    const int64_t w0 = (int64_t)blockIdx.x * kRoChunk;
     const int64_t w1 = min(W, w0 + kRoChunk);
     double re = 0.0, im = 0.0;
     for (int64_t base = w0; base < w1; base += kRoTile) {
@@ -347,8 +347,8 @@ readout_kernel(const Real *phase, const Real *phase_c, const Real *A, const Real
         __syncthreads();
     }
     if (combo <= n_combo) {
-        part[((int64_t)blockIdx.y * (n_combo + 1) + combo) * 2 + 0] = re;
-        part[((int64_t)blockIdx.y * (n_combo + 1) + combo) * 2 + 1] = im;
+        part[((int64_t)blockIdx.x * (n_combo + 1) + combo) * 2 + 0] = re;
+        part[((int64_t)blockIdx.x * (n_combo + 1) + combo) * 2 + 1] = im;
     }
 }
 
@@ -628,6 +628,8 @@ extern "C" rms_status rms_set_sequence(rms_substrate *sub, const rms_sequence_de
     if (!(d->dt_ms > 0.0) || !std::isfinite(d->dt_ms)) return fail(RMS_E_INVALID_ARG, "dt must be > 0");
     if (d->n_steps < 0 || d->n_steps > 2000000000ll) return fail(RMS_E_INVALID_ARG, "n_steps out of range");
     if (d->n_shapes < 1 || d->n_shapes > kMaxShapes) return fail(RMS_E_INVALID_ARG, "n_shapes must be 1..8");
+    if (d->n_dirs < 1 || d->n_b < 1 || (int64_t)d->n_shapes * d->n_dirs * d->n_b > 8000000)
+        return fail(RMS_E_INVALID_ARG, "n_shapes * n_dirs * n_b must be in 1..8e6");
     if ((d->n_steps > 0 && !d->G) || d->n_dirs < 1 || !d->dirs || d->n_b < 1 || !d->b || d->n_rec < 0 ||
         (d->n_rec > 0 && !d->rec_steps))
         return fail(RMS_E_INVALID_ARG, "missing waveform, directions, b-values or recording steps");
@@ -767,7 +769,7 @@ static rms_status finalize_impl(rms_run_handle *r)
                                                                                 r->n_blocks, r->d_mom);
         RMS_CUDA(cudaGetLastError());
     }
-    const dim3 rgrid((unsigned)((r->n_combo + 1 + kRoBlock - 1) / kRoBlock), (unsigned)r->n_chunks);
+    const dim3 rgrid((unsigned)r->n_chunks, (unsigned)((r->n_combo + 1 + kRoBlock - 1) / kRoBlock));
     readout_kernel<Real><<<rgrid, kRoBlock, 0, s>>>(st.phase, st.phase_c, st.A, st.A_c, r->W, q->S, q->d_q,
                                                     q->d_dirs, q->n_dirs, q->n_b, r->n_combo, r->d_ro_partial);
     readout_reduce_kernel<<<(r->n_combo + 1 + 127) / 128, 128, 0, s>>>(r->d_ro_partial, r->n_chunks, r->n_combo,

@@ -122,3 +122,28 @@ def test_voronoi_512cubed(rms):
     _check_sampled(oracle, wl, g64)
     g32 = rms.simulate(wl, rms.RMS_FP32, walkers=True)
     _check_fp32(wl, g64, g32)
+
+
+def test_three_hundred_million_walkers(rms):
+    """Past 2^28 walkers: 64-bit walker ids and indexing.  The signal of one
+    run of 3e8 walkers equals the merge of two shards of it (1e-12), and
+    walkers near the top of the id range match the oracle bit for bit."""
+    import oracle
+    import rms_inputs as ri
+    from paper_2012_06478_gb300 import shard
+    W = 300_000_000
+    wl = ri.workload("cylinder-32^3").with_(n_walkers=W, n_steps=20, G=ri.pgse(0.005, 0.01, 1e-3, 20)[None, :],
+                                            rec_steps=np.array([20]))
+    for prec in (rms.RMS_FP32, rms.RMS_FP64):
+        full = rms.simulate(wl, prec)
+        a = rms.simulate(wl, prec, n_walkers=W // 2)
+        b = rms.simulate(wl, prec, n_walkers=W - W // 2, walker_begin=W // 2)
+        v = shard.merge_in_rank_order([shard.pack_partials(a["S"], a["alpha_sum"], a["moments"]),
+                                       shard.pack_partials(b["S"], b["alpha_sum"], b["moments"])])
+        S, M, asum = shard.unpack_partials(v, full["S"].shape, full["moments"].shape)
+        np.testing.assert_allclose(S, full["S"], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(M, full["moments"], rtol=1e-12)
+    top = rms.simulate(wl, rms.RMS_FP64, n_walkers=64, walker_begin=W - 64, walkers=True)
+    o = oracle.run(wl, W - 64, W, n_threads=NT)
+    for k in ("i", "o", "c", "phase"):
+        np.testing.assert_array_equal(top[k], o[k].astype(top[k].dtype))
