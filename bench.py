@@ -304,7 +304,9 @@ def main():
     achieved = alg_bytes / (walk_launch_ms * 1e-3) / 1e9
     sm_mhz = (clk.summary().get("sm_mhz") or pk.get("sm_max_mhz") or 2070.0)
     lane_peak = ISSUE_LANES_PER_CLOCK * sm_mhz * 1e6
-    lane_rate = INST_PER_WALKER_STEP_FP32 * (W * spl) / (walk_launch_ms * 1e-3)
+    prof = PROFILED.get(wl.name, {})
+    lane_rate = (prof["inst_per_walker_step"] * (W * spl) / (walk_launch_ms * 1e-3)
+                 if "inst_per_walker_step" in prof else None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t32 / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -319,12 +321,13 @@ def main():
         "fp32_vs_fp64": fp32_err,
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if hbm else None, "traffic": TRAFFIC_PER_LAUNCH,
+                     "frac": (achieved / hbm) if hbm else None, "traffic": prof.get("traffic_per_launch"),
                      "kernel": "walk_kernel<float,1,false>", "alg_bytes_per_walker_step": 2.0 * eps,
                      "walker_steps_per_launch": W * spl, "launch_ms": walk_launch_ms,
                      "what": "label-lookup bytes (2 B per face event) against HBM copy bandwidth (of measured)"},
         "roofline_binding": {"bound": "alu", "achieved": lane_rate, "peak": lane_peak, "unit": "lane-instr/s",
-                             "frac": lane_rate / lane_peak, "inst_per_walker_step": INST_PER_WALKER_STEP_FP32,
+                             "frac": lane_rate / lane_peak if lane_rate else None,
+                             "inst_per_walker_step": prof.get("inst_per_walker_step"), "profile": prof.get("profile"),
                              "what": "issue slots: 152 SMs x 4 schedulers x 32 lanes x measured SM clock; work = "
                                      "thread-instructions per walker-step (ncu) x walker-steps/s of the walk launches"},
         "clocks": clk.summary(),
@@ -346,13 +349,14 @@ def main():
         dist.destroy_process_group()
 
 
-# Thread-instructions one walker-step of the FP32 walk kernel executes on the
-# axon workload (ncu: smsp__inst_executed x thread_inst_executed_per_inst_executed
-# / walker-steps; profiles/walk_kernel_fp32_axons-200x200x400.md).
-INST_PER_WALKER_STEP_FP32 = 355.1
-# DRAM bytes (read + write) of one walk launch of the benchmark workload (2000
-# steps x 1e6 walkers), from the same profile; None until measured.
-TRAFFIC_PER_LAUNCH = 153.1e6
+# Per workload, from the ncu capture of one FP32 walk launch of its benchmark
+# launch shape: thread-instructions per walker-step (smsp__inst_executed x
+# thread_inst_executed_per_inst_executed / walker-steps) and DRAM bytes read +
+# written per launch.  Workloads without a capture report null.
+PROFILED = {
+    "axons-200x200x400": {"inst_per_walker_step": 355.1, "traffic_per_launch": 153.1e6,
+                          "profile": "profiles/walk_kernel_fp32_axons-200x200x400.md"},
+}
 ISSUE_LANES_PER_CLOCK = 152 * 4 * 32  # SMs x schedulers x lanes
 
 
