@@ -58,7 +58,7 @@ class _Config(C.Structure):
         ("dt", C.c_double), ("n_steps", C.c_int64), ("n_shapes", C.c_int32),
         ("G", C.c_void_p), ("mode", C.c_void_p), ("n_rec", C.c_int32), ("rec_steps", C.c_void_p),
         ("seed", C.c_uint64), ("w_begin", C.c_int64), ("w_end", C.c_int64),
-        ("n_threads", C.c_int32), ("hash", C.c_int32),
+        ("n_threads", C.c_int32), ("hash", C.c_int32), ("interaction", C.c_int32),
     ]
 
 
@@ -185,6 +185,7 @@ def _config(wl, keep: _Keep, w_begin=0, w_end=None, n_threads=None, hash_=True,
     cfg.w_end = wl.n_walkers if w_end is None else w_end
     cfg.n_threads = n_threads or os.cpu_count() or 1
     cfg.hash = 1 if hash_ else 0
+    cfg.interaction = int(getattr(wl, "interaction", 0))
     return cfg
 
 

@@ -19,6 +19,12 @@
  *   - Sec. 2.1.4, Eq. 5: the weight alpha = exp(-sum_i t_i / T^(i)).
  *   - Sec. 2.3, Eq. 7: phase phi = int g(t).x(t) dt, S = <alpha e^{-i phi}>/<alpha>.
  *   - Sec. 2.3 (narrow-pulse D and K): alpha-weighted displacement moments.
+ *   - Sec. 2.1.2, App. A and B: two alternative particle-membrane interactions
+ *     the paper analyses for their bias.  Rejection sampling cancels a step
+ *     that a membrane refuses (the walker stays, the step's dt still counts
+ *     for relaxation); the equal-step-length random leap (ERL) cancels it and
+ *     draws a new direction until a step is admitted (at most 64 draws, then
+ *     the walker stays and an error bit is set).
  *
  * The paper does not print its kernel; the step is taken here in the order
  * and notation of Sec. 2.2, with every point where the text is silent fixed
@@ -131,7 +137,15 @@ typedef struct {
     int64_t w_begin, w_end;   /* global walker ids [w_begin, w_end) */
     int32_t n_threads;
     int32_t hash;             /* 1: keep the trajectory checksum */
+    int32_t interaction;      /* 0 elastic collision (Sec. 2.1.2-2.1.3), 1 rejection sampling
+                                 (App. B), 2 equal-step-length random leap (App. A) */
 } rmso_config;
+
+#define RMSO_EC 0
+#define RMSO_RS 1
+#define RMSO_ERL 2
+#define RMSO_MAX_LEAPS 64
+#define RMSO_ERR_LEAPS 16 /* an ERL step found no admissible direction in RMSO_MAX_LEAPS draws */
 
 typedef struct {
     /* per walker, index = w - w_begin */
@@ -390,15 +404,20 @@ static void direction_from(uint32_t x0, uint32_t x1, double n[3])
     n[2] = z;
 }
 
-/* The step's DIR call: direction from words 0, 1; PERM words 0, 1 from
- * words 2, 3. */
-static void direction(uint64_t seed, uint64_t w, uint32_t k, double n[3], uint32_t perm01[2])
+/* The step's DIR call (call = the attempt: 0, or the redraw of an ERL leap):
+ * direction from words 0, 1; PERM words 0, 1 from words 2, 3. */
+static void direction_call(uint64_t seed, uint64_t w, uint32_t k, uint32_t call, double n[3], uint32_t perm01[2])
 {
     uint32_t x[4];
-    draw(seed, w, k, TAG_DIR, 0u, x);
+    draw(seed, w, k, TAG_DIR, call, x);
     direction_from(x[0], x[1], n);
     perm01[0] = x[2];
     perm01[1] = x[3];
+}
+
+static void direction(uint64_t seed, uint64_t w, uint32_t k, double n[3], uint32_t perm01[2])
+{
+    direction_call(seed, w, k, 0u, n, perm01);
 }
 
 static double clamp01(double x)
@@ -434,8 +453,11 @@ static double clamp01(double x)
  * Finally every axis moves by (1 - tau) d and is clamped to [0,1].  The
  * relaxation exponent accumulates (segment duration) x (dt / T of the
  * segment's label). */
+#define WALK_REJECTED 1 /* walk_step: a membrane refused the step (rejection sampling or ERL) */
+
 static int walk_step(const ctx *X, uint64_t w, uint32_t k, walker *s, double n[3],
-                     const uint32_t perm01[2], const uint32_t *perm2_given, int mode)
+                     const uint32_t perm01[2], const uint32_t *perm2_given, int mode, int interaction,
+                     uint32_t attempt)
 {
     const rmso_config *cfg = X->cfg;
     const int L = cfg->n_labels;
@@ -501,7 +523,7 @@ static int walk_step(const ctx *X, uint64_t w, uint32_t k, walker *s, double n[3
                     word = *perm2_given;
                 } else {
                     uint32_t p4[4];
-                    draw(cfg->seed, w, k, TAG_PERM, 0u, p4);
+                    draw(cfg->seed, w, k, TAG_PERM, attempt, p4);
                     word = p4[0];
                 }
                 cross = word < Th;
@@ -526,6 +548,8 @@ static int walk_step(const ctx *X, uint64_t w, uint32_t k, walker *s, double n[3
                     }
                 }
             }
+        } else if (interaction != RMSO_EC) {
+            return WALK_REJECTED; /* the caller undoes the partial move */
         } else {
             n[best] = -n[best];
             d[best] = -d[best];
@@ -602,7 +626,32 @@ static void *run_range(void *arg)
             uint32_t perm01[2];
             direction(cfg->seed, (uint64_t)w, (uint32_t)k, n, perm01);
             int mode = cfg->mode ? cfg->mode[k - 1] : 0;
-            J->err |= walk_step(X, (uint64_t)w, (uint32_t)k, &s, n, perm01, NULL, mode);
+            if (cfg->interaction == RMSO_EC) {
+                walk_step(X, (uint64_t)w, (uint32_t)k, &s, n, perm01, NULL, mode, RMSO_EC, 0u);
+            } else {
+                /* App. B (rejection sampling): a step that a membrane refuses is
+                 * cancelled and the walker stays where it was for the step.
+                 * App. A (ERL): a refused step is cancelled and redrawn in a new
+                 * direction (DIR call = attempt) until one is admitted. */
+                const walker s0 = s;
+                const double rate0 = X->dtR[mode][s.c];
+                int accepted = 0;
+                const uint32_t attempts = cfg->interaction == RMSO_ERL ? RMSO_MAX_LEAPS : 1u;
+                for (uint32_t att = 0; att < attempts && !accepted; att++) {
+                    if (att > 0) {
+                        s = s0;
+                        direction_call(cfg->seed, (uint64_t)w, (uint32_t)k, att, n, perm01);
+                    }
+                    accepted = walk_step(X, (uint64_t)w, (uint32_t)k, &s, n, perm01, NULL, mode,
+                                         cfg->interaction, att) == 0;
+                }
+                if (!accepted) {
+                    s = s0; /* stays for the step, in its label */
+                    s.A = s.A + 1.0 * rate0;
+                    s.n_refl++;
+                    if (cfg->interaction == RMSO_ERL) J->err |= RMSO_ERR_LEAPS;
+                }
+            }
             if (cfg->hash) {
                 uint64_t v = (((uint64_t)k & 0xFFFFu) << 48) ^ ((uint64_t)(uint32_t)s.c << 32) ^
                              (uint64_t)flat_index(cfg, s.i);
@@ -773,7 +822,7 @@ int rmso_walk_once(const rmso_config *cfg, int64_t state_i[3], double state_o[3]
     }
     s.c = *c;
     s.A = *A;
-    err = walk_step(&X, 0u, 1u, &s, n, perm, perm + 2, mode);
+    err = walk_step(&X, 0u, 1u, &s, n, perm, perm + 2, mode, RMSO_EC, 0u);
     for (int a = 0; a < 3; a++) {
         state_i[a] = s.i[a];
         state_o[a] = s.o[a];

@@ -46,6 +46,8 @@ class Workload:
     b          float64 b-values (ms/um^2)
     rec_steps  int64 increasing recording steps in [1, n_steps]
     n_walkers, seed
+    interaction 0 elastic collision, 1 rejection sampling, 2 equal-step-length
+               random leap (the particle-membrane interaction of a run)
     """
     name: str
     labels: np.ndarray
@@ -65,6 +67,7 @@ class Workload:
     rec_steps: np.ndarray
     n_walkers: int
     seed: int
+    interaction: int = 0
 
     @property
     def n_labels(self) -> int:

@@ -17,7 +17,7 @@ def pytest_configure(config):
 
 def make_workload(labels, voxel_um=0.2, D=2.0, kappa=0.0, T2=math.inf, T1=math.inf, dt=1e-3,
                   n_steps=100, G=None, dirs=None, b=None, rec_steps=None, n_walkers=1000, seed=1,
-                  periodic=(1, 1, 1), dead=None, mode=None, name="test"):
+                  periodic=(1, 1, 1), dead=None, mode=None, name="test", interaction=0):
     """A Workload from per-label scalars or arrays (tests only)."""
     import rms_inputs as ri
     labels = np.ascontiguousarray(labels, dtype=np.uint16)
@@ -46,7 +46,8 @@ def make_workload(labels, voxel_um=0.2, D=2.0, kappa=0.0, T2=math.inf, T1=math.i
     dead = np.zeros(L, np.uint8) if dead is None else np.asarray(dead, np.uint8)
     return ri.Workload(name, labels, float(voxel_um), tuple(int(p) for p in periodic), Dv, T2v, T1v, K,
                        dead, float(dt), int(n_steps), G, mode, np.asarray(dirs, np.float64),
-                       np.asarray(b, np.float64), np.asarray(rec_steps, np.int64), int(n_walkers), int(seed))
+                       np.asarray(b, np.float64), np.asarray(rec_steps, np.int64), int(n_walkers), int(seed),
+                       int(interaction))
 
 
 @pytest.fixture(scope="session")
