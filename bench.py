@@ -101,9 +101,12 @@ def flush_l2(torch, buf):
     buf.add_(1.0)  # 256 MiB written: larger than the 129 MB L2
 
 
-def workload_of(name):
+INTERACTIONS = {"ec": 0, "rs": 1, "erl": 2}  # elastic collision, rejection sampling, ERL
+
+
+def workload_of(name, interaction="ec"):
     import rms_inputs as ri
-    return ri.workload(name)
+    return ri.workload(name).with_(interaction=INTERACTIONS[interaction])
 
 
 def events_per_step(wl):
@@ -140,7 +143,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = workload_of(args.workload)
+    wl = workload_of(args.workload, args.interaction)
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
@@ -161,7 +164,8 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "walkers_per_step": W, "steps_per_walker": wl.n_steps},
+            "config": {"workload": wl.name, "walkers_per_step": W, "steps_per_walker": wl.n_steps,
+                       "interaction": args.interaction},
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{W} walkers x {wl.n_steps} steps of {wl.name} per step"},
@@ -174,7 +178,7 @@ def ncu_case(args):
     workload's first `--ncu-case` steps, all walkers, one walk launch per form."""
     import torch
     import paper_2012_06478_gb300 as rms
-    wl = workload_of(args.workload)
+    wl = workload_of(args.workload, args.interaction)
     n = args.ncu_case
     wl = wl.with_(n_steps=n, G=np.asarray(wl.G)[:, :n], rec_steps=wl.rec_steps[wl.rec_steps <= n])
     for prec in (rms.RMS_FP32, rms.RMS_FP64):
@@ -189,6 +193,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--interaction", default="ec", choices=sorted(INTERACTIONS),
+                    help="particle-membrane interaction: elastic collision (the paper's method), rejection "
+                         "sampling or ERL (App. A, B)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64 plain-form steps")
     ap.add_argument("--fp64-warmup", type=int, default=1, help="untimed FP64 plain-form steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -216,7 +223,7 @@ def main():
 
     import paper_2012_06478_gb300 as rms
     from paper_2012_06478_gb300 import shard
-    wl = workload_of(args.workload)
+    wl = workload_of(args.workload, args.interaction)
     W = wl.n_walkers
     w_begin, _ = shard.shard_range(rank, world, W, weak=True)
     stream = torch.cuda.current_stream()
@@ -242,7 +249,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            run = rms.rms_run(seq, W, wl.seed, precision, 0, w_begin, 0, sp)
+            run = rms.rms_run(seq, W, wl.seed, precision, 0, w_begin, 0, sp, wl.interaction)
             e1.record(stream)
             res = rms.rms_read_signal(run)
             if it >= n_warm:
@@ -304,7 +311,7 @@ def main():
     achieved = alg_bytes / (walk_launch_ms * 1e-3) / 1e9
     sm_mhz = (clk.summary().get("sm_mhz") or pk.get("sm_max_mhz") or 2070.0)
     lane_peak = ISSUE_LANES_PER_CLOCK * sm_mhz * 1e6
-    prof = PROFILED.get(wl.name, {})
+    prof = PROFILED.get(wl.name if args.interaction == "ec" else f"{wl.name}/{args.interaction}", {})
     lane_rate = (prof["inst_per_walker_step"] * (W * spl) / (walk_launch_ms * 1e-3)
                  if "inst_per_walker_step" in prof else None)
     line = {
@@ -314,6 +321,7 @@ def main():
         "config": {"workload": wl.name, "walkers_per_gpu": W, "steps_per_walker": wl.n_steps, "dt_ms": wl.dt,
                    "grid_xyz": list(wl.shape_xyz), "voxel_um": wl.voxel_um, "labels": wl.n_labels,
                    "n_dirs": int(wl.dirs.shape[0]), "n_b": int(wl.b.size), "n_rec": int(wl.rec_steps.size),
+                   "interaction": args.interaction,
                    "precision": "fp32 form (headline); fp64 plain form in fp64_plain",
                    "l2": "flushed between timed iterations (256 MiB write)", "parallelism": f"walker shards x{world}"},
         "fp64_plain": {"value": value64, "unit": UNIT, "dtype": "f64", "steps": args.fp64_steps, "warmup": args.fp64_warmup,
@@ -322,7 +330,8 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if hbm else None, "traffic": prof.get("traffic_per_launch"),
-                     "kernel": "walk_kernel<float,1,false>", "alg_bytes_per_walker_step": 2.0 * eps,
+                     "kernel": f"walk_kernel<float,1,false,{INTERACTIONS[args.interaction]}>",
+                     "alg_bytes_per_walker_step": 2.0 * eps,
                      "walker_steps_per_launch": W * spl, "launch_ms": walk_launch_ms,
                      "what": "label-lookup bytes (2 B per face event) against HBM copy bandwidth (of measured)"},
         "roofline_binding": {"bound": "alu", "achieved": lane_rate, "peak": lane_peak, "unit": "lane-instr/s",
@@ -334,7 +343,7 @@ def main():
     }
     if not args.no_e2e:
         line["e2e"] = e2e(rms, torch, wl, W, w_begin, sp, args, world, max_over_ranks)
-    if not args.no_serving and world == 1:
+    if not args.no_serving and world == 1 and args.interaction == "ec":
         import rms_inputs as ri
         line["serving"] = serving(rms, ri, value, args.serving_requests, rms.RMS_FP32, sp)
         if args.serving_fp64 and value64:
@@ -442,7 +451,7 @@ def e2e(rms, torch, wl, W, w_begin, sp, args, world, max_over_ranks):
         sub = rms.rms_create_substrate(lab, wl.voxel_um, wl.D, T2=wl.T2, T1=wl.T1, kappa=wl.kappa, dead=wl.dead,
                                        periodic=wl.periodic, stream=sp)
         seq = rms.rms_set_sequence(sub, wl.dt, wl.G, wl.dirs, wl.b, wl.rec_steps, mode=wl.mode)
-        run = rms.rms_run(seq, W, wl.seed, rms.RMS_FP32, 0, w_begin, 0, sp)
+        run = rms.rms_run(seq, W, wl.seed, rms.RMS_FP32, 0, w_begin, 0, sp, wl.interaction)
         rms.rms_read_signal(run)
         el = time.perf_counter() - t0
         run.close()

@@ -41,6 +41,8 @@ typedef int rms_status;
 
 #define RMS_OK 0
 #define RMS_W_PROB_RANGE 1        /* warning: some P_{1->2} of Eq. 3 exceeded 1 and was clamped */
+#define RMS_W_LEAP_LIMIT 2        /* warning (RMS_ERL runs): some step found no admissible direction in
+                                     RMS_MAX_LEAPS draws; that walker stayed for the step (results valid) */
 #define RMS_E_INVALID_ARG (-1)    /* a null pointer, a size out of range, an inconsistent array */
 #define RMS_E_OOM (-2)            /* a device or host allocation failed */
 #define RMS_E_CUDA (-3)           /* a CUDA runtime call failed (message has the CUDA error) */
@@ -57,6 +59,27 @@ typedef int rms_status;
 
 /* rms_run flags */
 #define RMS_TRAJ_HASH 1u /* keep a per-walker 64-bit checksum of the (step, voxel, label) sequence */
+
+/* Particle-membrane interaction of rms_run (Sec. 2.1.2).  A face is "refused"
+ * when it is impermeable (a label pair with kappa = 0, a dead label, the wall
+ * beyond a non-periodic edge) or when the Bernoulli trial of Eq. 3 fails.
+ *   RMS_EC  elastic collision: a refused face reflects the step specularly
+ *           and the rest of the step goes on (the paper's method).
+ *   RMS_RS  rejection sampling (App. B): a refused face cancels the whole
+ *           step; the walker stays where it was for that step (its dt still
+ *           counts in the relaxation exponent of Eq. 5).
+ *   RMS_ERL equal-step-length random leap (App. A): a refused face cancels
+ *           the step and a new direction is drawn, until a step meets no
+ *           refused face; draw m (m = 0, 1, ...) takes Philox DIR call m and
+ *           PERM call m.  After RMS_MAX_LEAPS refused draws the walker stays
+ *           for the step, as in RMS_RS, and the run reports RMS_W_LEAP_LIMIT.
+ * App. A and B show that RS biases D parallel to membranes and that ERL also
+ * makes the density near membranes inhomogeneous; they are here to reproduce
+ * those biases and to compare against other simulators. */
+#define RMS_EC 0
+#define RMS_RS 1
+#define RMS_ERL 2
+#define RMS_MAX_LEAPS 64
 
 typedef struct rms_substrate rms_substrate;
 typedef struct rms_sequence rms_sequence;
@@ -146,13 +169,15 @@ typedef struct {
     int32_t precision;        /* RMS_FP64 or RMS_FP32 */
     uint32_t flags;           /* RMS_TRAJ_HASH or 0 */
     int32_t steps_per_launch; /* steps per kernel launch (0 = default) */
+    int32_t interaction;      /* RMS_EC (0), RMS_RS or RMS_ERL */
     void *stream;             /* cudaStream_t the whole run is enqueued on */
 } rms_run_desc;
 
 /* Allocate walker state and enqueue the whole simulation: initialisation
- * (Sec. 2.2 item 1), every step (Sec. 2.2 items 2-5), the moment reductions
- * and the signal read-out (Eq. 7).  Returns without waiting.  Errors:
- * RMS_E_INVALID_ARG, RMS_E_OOM, RMS_E_CUDA. */
+ * (Sec. 2.2 item 1), every step (Sec. 2.2 items 2-5, with the interaction
+ * desc->interaction), the moment reductions and the signal read-out (Eq. 7).
+ * Returns without waiting.  Errors: RMS_E_INVALID_ARG (also an unknown
+ * interaction), RMS_E_OOM, RMS_E_CUDA. */
 rms_status rms_run(rms_sequence *seq, const rms_run_desc *desc, rms_run_handle **out);
 
 /* RMS_OK when the run has finished, RMS_E_NOT_READY while in flight. */
@@ -162,7 +187,9 @@ rms_status rms_run_query(rms_run_handle *run);
  * returns RMS_E_CANCELLED. */
 rms_status rms_cancel(rms_run_handle *run);
 
-/* Wait for the run and copy results to host memory (any pointer may be NULL):
+/* Wait for the run and copy results to host memory (any pointer may be NULL).
+ * Returns RMS_OK, or RMS_W_LEAP_LIMIT (results valid) for an RMS_ERL run in
+ * which some step used up its draws:
  *   S_re, S_im : n_shapes*n_dirs*n_b, S = sum alpha e^{-i phi} / sum alpha
  *                (index (shape*n_dirs + dir)*n_b + b)
  *   moments    : n_rec*22 unnormalised sums over walkers at each recording step
@@ -174,7 +201,7 @@ rms_status rms_read_signal(rms_run_handle *run, double *S_re, double *S_im, doub
                            double *alpha_sum);
 
 /* Wait for the run and copy the final per-walker state to host memory (any
- * pointer may be NULL): i (W*3 int32 unwrapped voxel index), o (W*3 double
+ * pointer may be NULL; return codes as rms_read_signal): i (W*3 int32 unwrapped voxel index), o (W*3 double
  * offset in [0,1]; the FP32 form's offsets widened), i0 (W*3), o0 (W*3),
  * c (W int32 label), A (W double exponent of Eq. 5), phase (W*n_shapes*3
  * double, sum_k dt G_k dx_k in um ms), hash (W uint64, RMS_TRAJ_HASH runs). */
@@ -209,8 +236,9 @@ rms_status rms_server_create(const rms_server_config *cfg, rms_server **out);
 
 /* Queue a request: n_walkers walkers of `seq` (its substrate stays resident;
  * both must outlive the request -- destroying them returns RMS_E_BUSY
- * meanwhile), Philox key `seed`, RMS_FP64 or RMS_FP32.  Returns at once with
- * a ticket.  The result equals rms_run's for the same arguments. */
+ * meanwhile), Philox key `seed`, RMS_FP64 or RMS_FP32, elastic collision
+ * (RMS_EC).  Returns at once with a ticket.  The result equals rms_run's for
+ * the same arguments. */
 rms_status rms_server_submit(rms_server *srv, rms_sequence *seq, int64_t n_walkers, uint64_t seed,
                              int32_t precision, int64_t *ticket);
 

@@ -12,6 +12,7 @@ LIB_PATH = os.path.join(HERE, "librms.so")
 
 RMS_OK = 0
 RMS_W_PROB_RANGE = 1
+RMS_W_LEAP_LIMIT = 2
 RMS_E_INVALID_ARG = -1
 RMS_E_OOM = -2
 RMS_E_CUDA = -3
@@ -24,6 +25,10 @@ RMS_E_NOT_READY = -10
 RMS_FP64 = 0
 RMS_FP32 = 1
 RMS_TRAJ_HASH = 1
+RMS_EC = 0
+RMS_RS = 1
+RMS_ERL = 2
+RMS_MAX_LEAPS = 64
 
 
 class RmsError(RuntimeError):
@@ -53,7 +58,7 @@ class ServerConfig(C.Structure):
 class RunDesc(C.Structure):
     _fields_ = [("n_walkers", C.c_int64), ("walker_begin", C.c_int64), ("seed", C.c_uint64),
                 ("precision", C.c_int32), ("flags", C.c_uint32), ("steps_per_launch", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("interaction", C.c_int32), ("stream", C.c_void_p)]
 
 
 # name -> (argtypes, restype); the exported C entry points of include/rms.h

@@ -17,12 +17,13 @@ from typing import Optional, Sequence as Seq
 import numpy as np
 
 from . import _lib as L
-from ._lib import RMS_FP32, RMS_FP64, RMS_TRAJ_HASH, RmsError, check
+from ._lib import RMS_EC, RMS_ERL, RMS_FP32, RMS_FP64, RMS_RS, RMS_TRAJ_HASH, RmsError, check
 
 __all__ = ["rms_create_substrate", "rms_set_sequence", "rms_run", "rms_read_signal", "rms_read_walkers",
            "rms_cancel", "rms_run_query", "rms_destroy_run", "rms_destroy_sequence", "rms_destroy_substrate",
            "rms_sequence_bvalues", "rms_run_step_time_ms", "simulate", "current_stream",
-           "RMS_FP32", "RMS_FP64", "RMS_TRAJ_HASH", "RmsError", "MOMENT_NAMES", "Server"]
+           "RMS_FP32", "RMS_FP64", "RMS_TRAJ_HASH", "RMS_EC", "RMS_RS", "RMS_ERL", "RmsError", "MOMENT_NAMES",
+           "Server"]
 
 MOMENT_NAMES = ["1", "xx", "xy", "xz", "yy", "yz", "zz", "xxxx", "xxxy", "xxxz", "xxyy", "xxyz", "xxzz", "xyyy",
                 "xyyz", "xyzz", "xzzz", "yyyy", "yyyz", "yyzz", "yzzz", "zzzz"]
@@ -86,12 +87,14 @@ class Sequence:
 
 
 class Run:
-    def __init__(self, handle, seq, n_walkers, precision, flags):
+    def __init__(self, handle, seq, n_walkers, precision, flags, interaction=RMS_EC):
         self.handle = handle
         self.seq = seq
         self.n_walkers = n_walkers
         self.precision = precision
         self.flags = flags
+        self.interaction = interaction
+        self.status = L.RMS_OK  # RMS_W_LEAP_LIMIT once a read reports it
 
     def close(self):
         if self.handle:
@@ -173,7 +176,8 @@ def rms_sequence_bvalues(seq: Sequence) -> np.ndarray:
 
 
 def rms_run(seq: Sequence, n_walkers: int, seed: int, precision: int = RMS_FP64, flags: int = 0,
-            walker_begin: int = 0, steps_per_launch: int = 0, stream: Optional[int] = None) -> Run:
+            walker_begin: int = 0, steps_per_launch: int = 0, stream: Optional[int] = None,
+            interaction: int = RMS_EC) -> Run:
     d = L.RunDesc()
     d.n_walkers = int(n_walkers)
     d.walker_begin = int(walker_begin)
@@ -181,10 +185,11 @@ def rms_run(seq: Sequence, n_walkers: int, seed: int, precision: int = RMS_FP64,
     d.precision = int(precision)
     d.flags = int(flags)
     d.steps_per_launch = int(steps_per_launch)
+    d.interaction = int(interaction)
     d.stream = current_stream() if stream is None else stream
     h = C.c_void_p()
     check(L.lib.rms_run(seq.handle, C.byref(d), C.byref(h)))
-    return Run(h, seq, int(n_walkers), precision, flags)
+    return Run(h, seq, int(n_walkers), precision, flags, int(interaction))
 
 
 def rms_run_query(run: Run) -> bool:
@@ -203,8 +208,9 @@ def rms_read_signal(run: Run):
     re, im = np.zeros(n), np.zeros(n)
     mom = np.zeros((q.n_rec, 22))
     asum = np.zeros(1)
-    check(L.lib.rms_read_signal(run.handle, re.ctypes.data, im.ctypes.data, mom.ctypes.data if q.n_rec else None,
-                                asum.ctypes.data))
+    run.status = check(L.lib.rms_read_signal(run.handle, re.ctypes.data, im.ctypes.data,
+                                             mom.ctypes.data if q.n_rec else None, asum.ctypes.data),
+                       allow=(L.RMS_OK, L.RMS_W_LEAP_LIMIT))
     return (re + 1j * im).reshape(q.n_shapes, q.n_dirs, q.n_b), mom, float(asum[0])
 
 
@@ -213,8 +219,9 @@ def rms_read_walkers(run: Run) -> dict:
     out = dict(i=np.zeros((W, 3), np.int32), o=np.zeros((W, 3)), i0=np.zeros((W, 3), np.int32),
                o0=np.zeros((W, 3)), c=np.zeros(W, np.int32), A=np.zeros(W), phase=np.zeros((W, S, 3)),
                hash=np.zeros(W, np.uint64))
-    check(L.lib.rms_read_walkers(run.handle, *[out[k].ctypes.data for k in
-                                               ("i", "o", "i0", "o0", "c", "A", "phase", "hash")]))
+    run.status = check(L.lib.rms_read_walkers(run.handle, *[out[k].ctypes.data for k in
+                                                            ("i", "o", "i0", "o0", "c", "A", "phase", "hash")]),
+                       allow=(L.RMS_OK, L.RMS_W_LEAP_LIMIT))
     return out
 
 
@@ -238,18 +245,21 @@ def rms_destroy_substrate(sub: Substrate) -> None:
 
 def simulate(wl, precision: int = RMS_FP64, n_walkers: Optional[int] = None, seed: Optional[int] = None,
              hash_: bool = False, walker_begin: int = 0, steps_per_launch: int = 0, walkers: bool = False,
-             stream: Optional[int] = None) -> dict:
-    """Run one workload (an rms_inputs.Workload) end to end through the C ABI."""
+             stream: Optional[int] = None, interaction: Optional[int] = None) -> dict:
+    """Run one workload (an rms_inputs.Workload) end to end through the C ABI.
+    The interaction defaults to the workload's (elastic collision if unset);
+    `leap_limit` in the result is True when an ERL step used up its draws."""
     sub = rms_create_substrate(wl.labels, wl.voxel_um, wl.D, T2=wl.T2, T1=wl.T1, kappa=wl.kappa, dead=wl.dead,
                                periodic=wl.periodic, stream=stream)
     G = np.asarray(wl.G, np.float64)
     G = G.reshape(-1, wl.n_steps) if wl.n_steps else np.zeros((G.shape[0] if G.ndim == 2 else 1, 0))
     seq = rms_set_sequence(sub, wl.dt, G, wl.dirs, wl.b, wl.rec_steps, mode=wl.mode)
     run = rms_run(seq, wl.n_walkers if n_walkers is None else n_walkers, wl.seed if seed is None else seed,
-                  precision, RMS_TRAJ_HASH if hash_ else 0, walker_begin, steps_per_launch, stream)
+                  precision, RMS_TRAJ_HASH if hash_ else 0, walker_begin, steps_per_launch, stream,
+                  int(getattr(wl, "interaction", RMS_EC)) if interaction is None else int(interaction))
     S, mom, asum = rms_read_signal(run)
     res = dict(S=S, moments=mom, alpha_sum=asum, status=seq.status, step_ms=rms_run_step_time_ms(run),
-               b_s=rms_sequence_bvalues(seq))
+               b_s=rms_sequence_bvalues(seq), leap_limit=run.status == L.RMS_W_LEAP_LIMIT)
     if walkers:
         res.update(rms_read_walkers(run))
     run.close()

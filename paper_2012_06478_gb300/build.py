@@ -2,8 +2,8 @@
 
 The plain FP64 form and the C-ABI/set-up/read-out unit are compiled with
 -fmad=false (no FMA contraction, so every operation rounds as in the CPU
-reference); the FP32 form keeps FMA contraction.  The three translation
-units compile in parallel; the link uses nvcc's static CUDA runtime.
+reference); the FP32 forms keep FMA contraction.  The translation units
+compile in parallel; the link uses nvcc's static CUDA runtime.
 """
 from __future__ import annotations
 
@@ -20,6 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
           "--expt-relaxed-constexpr"]
 UNITS = [("rms_api.cu", ["-fmad=false"]), ("walk_fp64.cu", ["-fmad=false"]), ("walk_fp32.cu", ["-fmad=true"]),
+         ("walk_reject_fp64.cu", ["-fmad=false"]), ("walk_reject_fp32.cu", ["-fmad=true"]),
          ("rms_noalloc.cu", ["-fmad=false"]), ("rms_serve.cu", ["-fmad=false"])]
 
 

@@ -747,8 +747,19 @@ template <typename Real>
 static rms_status walk_impl(rms_run_handle *r, int64_t k0, int64_t k1)
 {
     const ReqDesc<Real> d = run_desc<Real>(r);
-    RMS_CUDA(launch_walk<Real>(r->seq->S, (r->flags & RMS_TRAJ_HASH) != 0, dim3((unsigned)r->n_blocks), r->stream,
-                               d.g, d.t, d.st, d.ctl, k0, k1));
+    const bool hash = (r->flags & RMS_TRAJ_HASH) != 0;
+    const dim3 grid((unsigned)r->n_blocks);
+    const int S = r->seq->S;
+    switch (r->interaction) {
+    case RMS_RS:
+        RMS_CUDA((launch_walk<Real, kInteractRS>(S, hash, grid, r->stream, d.g, d.t, d.st, d.ctl, k0, k1)));
+        break;
+    case RMS_ERL:
+        RMS_CUDA((launch_walk<Real, kInteractERL>(S, hash, grid, r->stream, d.g, d.t, d.st, d.ctl, k0, k1)));
+        break;
+    default:
+        RMS_CUDA((launch_walk<Real, kInteractEC>(S, hash, grid, r->stream, d.g, d.t, d.st, d.ctl, k0, k1)));
+    }
     return RMS_OK;
 }
 
@@ -866,6 +877,8 @@ extern "C" rms_status rms_run(rms_sequence *q, const rms_run_desc *d, rms_run_ha
         return fail(RMS_E_INVALID_ARG, "precision must be RMS_FP64 or RMS_FP32");
     if (d->flags & ~RMS_TRAJ_HASH) return fail(RMS_E_INVALID_ARG, "unknown flag");
     if (d->steps_per_launch < 0) return fail(RMS_E_INVALID_ARG, "steps_per_launch must be >= 0");
+    if (d->interaction != RMS_EC && d->interaction != RMS_RS && d->interaction != RMS_ERL)
+        return fail(RMS_E_INVALID_ARG, "interaction must be RMS_EC, RMS_RS or RMS_ERL");
     rms_run_handle *r = new (std::nothrow) rms_run_handle();
     if (!r) return fail(RMS_E_OOM, "host allocation");
     r->seq = q;
@@ -874,6 +887,7 @@ extern "C" rms_status rms_run(rms_sequence *q, const rms_run_desc *d, rms_run_ha
     r->seed = d->seed;
     r->precision = d->precision;
     r->flags = d->flags;
+    r->interaction = d->interaction;
     r->stream = (cudaStream_t)d->stream;
     int32_t spl = d->steps_per_launch;
     if (spl == 0) {
@@ -913,14 +927,20 @@ static rms_status finish(rms_run_handle *r)
     if (*(volatile int32_t *)r->h_cancel) return fail(RMS_E_CANCELLED, "run was cancelled");
     int32_t status = 0;
     RMS_CUDA(cudaMemcpy(&status, r->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
-    if (status) return fail(RMS_E_DEVICE, "device status " + std::to_string(status));
+    if (status & ~kWarnLeaps) return fail(RMS_E_DEVICE, "device status " + std::to_string(status));
+    if (status & kWarnLeaps) {
+        set_last_error("an ERL step found no admissible direction in RMS_MAX_LEAPS draws; "
+                       "that walker stayed for the step");
+        return RMS_W_LEAP_LIMIT;
+    }
     return RMS_OK;
 }
 
 extern "C" rms_status rms_read_signal(rms_run_handle *r, double *S_re, double *S_im, double *moments, double *alpha_sum)
 {
     if (!r) return fail(RMS_E_INVALID_ARG, "null run");
-    RMS_TRY(finish(r));
+    const rms_status fin = finish(r);
+    if (fin < 0) return fin;
     std::vector<double> S((size_t)2 * (r->n_combo + 1));
     RMS_CUDA(cudaMemcpy(S.data(), r->d_S, sizeof(double) * S.size(), cudaMemcpyDeviceToHost));
     for (int k = 0; k < r->n_combo; ++k) {
@@ -930,14 +950,15 @@ extern "C" rms_status rms_read_signal(rms_run_handle *r, double *S_re, double *S
     if (alpha_sum) *alpha_sum = S[2 * r->n_combo];
     if (moments && r->seq->n_rec > 0)
         RMS_CUDA(cudaMemcpy(moments, r->d_mom, sizeof(double) * r->seq->n_rec * kMoments, cudaMemcpyDeviceToHost));
-    return RMS_OK;
+    return fin;
 }
 
 extern "C" rms_status rms_read_walkers(rms_run_handle *r, int32_t *i, double *o, int32_t *i0, double *o0, int32_t *c,
                                        double *A, double *phase, uint64_t *hash)
 {
     if (!r) return fail(RMS_E_INVALID_ARG, "null run");
-    RMS_TRY(finish(r));
+    const rms_status fin = finish(r);
+    if (fin < 0) return fin;
     const int64_t W = r->W;
     const int S = r->seq->S;
     cudaStream_t s = r->stream;
@@ -975,7 +996,7 @@ extern "C" rms_status rms_read_walkers(rms_run_handle *r, int32_t *i, double *o,
         if (x.h) RMS_CUDA(cudaMemcpyAsync(x.h, x.d, x.n, cudaMemcpyDeviceToHost, s));
     RMS_CUDA(cudaFreeAsync(buf, s));
     RMS_CUDA(cudaStreamSynchronize(s));
-    return RMS_OK;
+    return fin;
 }
 
 extern "C" rms_status rms_run_step_time_ms(rms_run_handle *r, float *ms)

@@ -82,8 +82,13 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z)
 constexpr int kMoments = 22;  // alpha, 6 second-order, 15 fourth-order terms
 constexpr int kMaxShapes = 8;
 
-// Device error bits (status word).
-enum : int { kErrTimeout = 4 };
+// Device status bits: errors, and one warning (an ERL step that found no
+// admissible direction in kMaxLeaps draws; the walker stayed for that step).
+enum : int { kErrTimeout = 4, kWarnLeaps = 8 };
+
+// Particle-membrane interaction (Sec. 2.1.2, App. A and B).
+enum : int { kInteractEC = 0, kInteractRS = 1, kInteractERL = 2 };
+constexpr uint32_t kMaxLeaps = 64;  // ERL draws per step
 
 // Walker state, structure of arrays, one entry per walker.
 template <typename Real>

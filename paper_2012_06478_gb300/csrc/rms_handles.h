@@ -50,6 +50,7 @@ struct rms_run_handle {
     uint64_t seed = 0;
     int32_t precision = RMS_FP64;
     uint32_t flags = 0;
+    int32_t interaction = RMS_EC;
     cudaStream_t stream = nullptr;
     int32_t n_blocks = 0;
     char *d_state = nullptr;  // one allocation for the walker state

@@ -7,17 +7,22 @@
 
 namespace rms {
 
-template <typename Real>
+template <typename Real, int IM>
 cudaError_t launch_walk(int n_shapes, bool hash, dim3 grid, cudaStream_t stream, const Geometry &g,
                         const Tables<Real> &t, const WalkerState<Real> &st, const RunCtl &ctl,
                         int64_t k_begin, int64_t k_end);
 
-extern template cudaError_t launch_walk<double>(int, bool, dim3, cudaStream_t, const Geometry &,
-                                                const Tables<double> &, const WalkerState<double> &,
-                                                const RunCtl &, int64_t, int64_t);
-extern template cudaError_t launch_walk<float>(int, bool, dim3, cudaStream_t, const Geometry &,
-                                               const Tables<float> &, const WalkerState<float> &,
-                                               const RunCtl &, int64_t, int64_t);
+#define RMS_EXTERN_LAUNCH_WALK(REAL, IM)                                                                   \
+    extern template cudaError_t launch_walk<REAL, IM>(int, bool, dim3, cudaStream_t, const Geometry &,    \
+                                                      const Tables<REAL> &, const WalkerState<REAL> &,    \
+                                                      const RunCtl &, int64_t, int64_t);
+RMS_EXTERN_LAUNCH_WALK(double, kInteractEC)
+RMS_EXTERN_LAUNCH_WALK(double, kInteractRS)
+RMS_EXTERN_LAUNCH_WALK(double, kInteractERL)
+RMS_EXTERN_LAUNCH_WALK(float, kInteractEC)
+RMS_EXTERN_LAUNCH_WALK(float, kInteractRS)
+RMS_EXTERN_LAUNCH_WALK(float, kInteractERL)
+#undef RMS_EXTERN_LAUNCH_WALK
 
 template <typename Real>
 cudaError_t launch_walk_batched(int ns_bucket, int32_t n_tasks, cudaStream_t stream, const ReqDesc<Real> *reqs,

@@ -171,8 +171,13 @@ __device__ __forceinline__ void warp_moments(double al, const double dx[3], doub
 }
 
 // Steps (k_begin, k_end] for the kWalkBlock walkers of block `block` of a
-// run (walkers block*kWalkBlock ...), one walker per thread.
-template <typename Real, int NS, bool HASH>
+// run (walkers block*kWalkBlock ...), one walker per thread.  IM is the
+// particle-membrane interaction: elastic collision (Sec. 2.1.2-2.1.3, the
+// paper's method), or one of the alternatives of App. A and B, in which a
+// refused face cancels the step -- rejection sampling keeps the walker where
+// it was for the step, ERL draws a new direction (DIR and PERM call = the
+// draw's index) until a step is admitted, at most kMaxLeaps draws.
+template <typename Real, int NS, bool HASH, int IM>
 __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real> &t, const WalkerState<Real> &st,
                                            const RunCtl &ctl, int64_t block, int64_t k_begin, int64_t k_end)
 {
@@ -235,16 +240,36 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
     for (int64_t k = k_begin + 1; k <= k_end; ++k) {
         const uint8_t fl = __ldg(t.flags + (k - 1));
         if (active) {
+            const int mode = t.mode ? (int)__ldg(t.mode + (k - 1)) : 0;
+            // state at the step start, restored when a membrane refuses the step
+            [[maybe_unused]] Real o_s[3], A_s, Ac_s;
+            [[maybe_unused]] int32_t wc_s[3], di_s[3], v_s, c_s;
+            if constexpr (IM != kInteractEC) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    o_s[a] = o[a];
+                    wc_s[a] = wc[a];
+                    di_s[a] = di[a];
+                }
+                v_s = v;
+                c_s = c;
+                A_s = A;
+                Ac_s = Ac;
+            }
+            uint32_t att = 0;  // draw index (ERL redraws); always 0 otherwise
+#pragma unroll 1
+            for (;;) {
             // ---- direction (one DIR call: words 0, 1 -> direction; words 2, 3 ->
             //      the Bernoulli words of the step's first two membrane events)
-            const U4 x = draw(ctl.seed, w, (uint32_t)k, kTagDir, 0u);
+            const U4 x = draw(ctl.seed, w, (uint32_t)k, kTagDir, att);
             Real n[3];
             direction_from(x.x, x.y, t.trig, n);
             // ---- face walk (Sec. 2.2 items 3-4)
-            const int mode = t.mode ? (int)__ldg(t.mode + (k - 1)) : 0;
             Real sc = __ldg(t.s + c);
             Real rate = t.any_relax ? __ldg(t.dtR + mode * L + c) : Real(0);
+            [[maybe_unused]] const Real rate0 = rate;
             Real d[3] = {n[0] * sc, n[1] * sc, n[2] * sc};
+            [[maybe_unused]] bool refused = false;
             // A face event on axis `best` moving up/down: look up the voxel across
             // it and decide between crossing and reflection.
             auto face = [&](int best, bool up, int ev) -> bool {
@@ -289,7 +314,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                     } else {
                         // third membrane event of a step: word 0 of the step's PERM call
                         const uint32_t word =
-                            ev == 0 ? x.z : (ev == 1 ? x.w : draw(ctl.seed, w, (uint32_t)k, kTagPerm, 0u).x);
+                            ev == 0 ? x.z : (ev == 1 ? x.w : draw(ctl.seed, w, (uint32_t)k, kTagPerm, att).x);
                         cross = word < T;
                     }
                 }
@@ -307,6 +332,8 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                         if (t.any_relax) rate = __ldg(t.dtR + mode * L + c);
                         return true;  // the caller switches to the new label's step length
                     }
+                } else if constexpr (IM != kInteractEC) {
+                    refused = true;
                 } else {
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
@@ -364,7 +391,11 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                     }
                     if (t.any_relax) A = A + dts * rate;
                     tau = tmin;
-                    if (face(best, up, ev)) {
+                    const bool changed = face(best, up, ev);
+                    if constexpr (IM != kInteractEC) {
+                        if (refused) break;
+                    }
+                    if (changed) {
                         const double sn = __ldg(t.s + c);
                         if (dbits(sn) != dbits(sc)) {
                             sc = sn;
@@ -377,10 +408,12 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                         }
                     }
                 }
-                const double rem = 1.0 - tau;
+                if (IM == kInteractEC || !refused) {
+                    const double rem = 1.0 - tau;
 #pragma unroll
-                for (int a = 0; a < 3; ++a) o[a] = dclamp01(o[a] + rem * d[a]);
-                if (t.any_relax) A = A + rem * rate;
+                    for (int a = 0; a < 3; ++a) o[a] = dclamp01(o[a] + rem * d[a]);
+                    if (t.any_relax) A = A + rem * rate;
+                }
             } else {
                 // Precision form: the same walk in FP32 (approximate division).
                 constexpr Real kNever = Real(1e30);
@@ -420,7 +453,11 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                     }
                     if (t.any_relax) kahan_add(A, Ac, dtt * rate);
                     tau = tmin;
-                    if (face(best, up, ev)) {
+                    const bool changed = face(best, up, ev);
+                    if constexpr (IM != kInteractEC) {
+                        if (refused) break;
+                    }
+                    if (changed) {
                         const Real sn = __ldg(t.s + c);
                         if (sn != sc) {
                             sc = sn;
@@ -434,11 +471,40 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                         }
                     }
                 }
-                const Real rem = Real(1) - tau;
+                if (IM == kInteractEC || !refused) {
+                    const Real rem = Real(1) - tau;
 #pragma unroll
-                for (int a = 0; a < 3; ++a) o[a] = clamp01(o[a] + rem * d[a]);
-                if (t.any_relax) kahan_add(A, Ac, rem * rate);
+                    for (int a = 0; a < 3; ++a) o[a] = clamp01(o[a] + rem * d[a]);
+                    if (t.any_relax) kahan_add(A, Ac, rem * rate);
+                }
             }
+            if constexpr (IM == kInteractEC) {
+                break;
+            } else {
+                if (!refused) break;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    o[a] = o_s[a];
+                    wc[a] = wc_s[a];
+                    di[a] = di_s[a];
+                }
+                v = v_s;
+                c = c_s;
+                A = A_s;
+                Ac = Ac_s;
+                if (IM == kInteractRS || ++att >= kMaxLeaps) {
+                    // the walker stays for the step, in its label
+                    if (t.any_relax) {
+                        if constexpr (kF64)
+                            A = A + rate0;
+                        else
+                            kahan_add(A, Ac, rate0);
+                    }
+                    if (IM == kInteractERL) atomicOr(ctl.status, kWarnLeaps);
+                    break;
+                }
+            }
+            }  // draws
             if (HASH) {
                 const uint64_t x = (((uint64_t)k & 0xFFFFu) << 48) ^ ((uint64_t)(uint32_t)c << 32) ^
                                    (uint64_t)(uint32_t)v;
@@ -510,11 +576,11 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
 }
 
 // One run: block b of the grid advances walkers b*kWalkBlock ... of the run.
-template <typename Real, int NS, bool HASH>
+template <typename Real, int NS, bool HASH, int IM>
 __global__ void __launch_bounds__(kWalkBlock)
 walk_kernel(Geometry g, Tables<Real> t, WalkerState<Real> st, RunCtl ctl, int64_t k_begin, int64_t k_end)
 {
-    walk_block<Real, NS, HASH>(g, t, st, ctl, blockIdx.x, k_begin, k_end);
+    walk_block<Real, NS, HASH, IM>(g, t, st, ctl, blockIdx.x, k_begin, k_end);
 }
 
 // Many runs in one launch (continuous batching): block i executes task i --
@@ -532,7 +598,8 @@ walk_batched_kernel(const ReqDesc<Real> *reqs, const BlockTask *tasks, int32_t n
         s_req = reqs[s_task.req];
     }
     __syncthreads();
-    walk_block<Real, NS, false>(s_req.g, s_req.t, s_req.st, s_req.ctl, s_task.block, s_task.k0, s_task.k1);
+    walk_block<Real, NS, false, kInteractEC>(s_req.g, s_req.t, s_req.st, s_req.ctl, s_task.block, s_task.k0,
+                                             s_task.k1);
 }
 
 template <typename Real>
@@ -552,20 +619,22 @@ cudaError_t launch_walk_batched(int ns_bucket, int32_t n_tasks, cudaStream_t str
     return cudaGetLastError();
 }
 
-// Host-side launcher, instantiated in walk_fp64.cu / walk_fp32.cu.
-template <typename Real>
+// Host-side launcher for interaction IM, instantiated in walk_fp64.cu /
+// walk_fp32.cu (elastic collision) and walk_reject_fp64.cu /
+// walk_reject_fp32.cu (rejection sampling, ERL).
+template <typename Real, int IM>
 cudaError_t launch_walk(int n_shapes, bool hash, dim3 grid, cudaStream_t stream, const Geometry &g,
                         const Tables<Real> &t, const WalkerState<Real> &st, const RunCtl &ctl,
                         int64_t k_begin, int64_t k_end)
 {
-#define RMS_LAUNCH(NSV)                                                                          \
-    do {                                                                                         \
-        if (hash)                                                                                \
-            walk_kernel<Real, NSV, true><<<grid, kWalkBlock, 0, stream>>>(g, t, st, ctl, k_begin, \
-                                                                         k_end);                 \
-        else                                                                                     \
-            walk_kernel<Real, NSV, false><<<grid, kWalkBlock, 0, stream>>>(g, t, st, ctl,        \
-                                                                          k_begin, k_end);       \
+#define RMS_LAUNCH(NSV)                                                                              \
+    do {                                                                                             \
+        if (hash)                                                                                    \
+            walk_kernel<Real, NSV, true, IM><<<grid, kWalkBlock, 0, stream>>>(g, t, st, ctl, k_begin, \
+                                                                             k_end);                 \
+        else                                                                                         \
+            walk_kernel<Real, NSV, false, IM><<<grid, kWalkBlock, 0, stream>>>(g, t, st, ctl,        \
+                                                                              k_begin, k_end);       \
     } while (0)
     if (n_shapes <= 1)
         RMS_LAUNCH(1);
