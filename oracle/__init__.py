@@ -59,6 +59,7 @@ class _Config(C.Structure):
         ("G", C.c_void_p), ("mode", C.c_void_p), ("n_rec", C.c_int32), ("rec_steps", C.c_void_p),
         ("seed", C.c_uint64), ("w_begin", C.c_int64), ("w_end", C.c_int64),
         ("n_threads", C.c_int32), ("hash", C.c_int32), ("interaction", C.c_int32),
+        ("rho", C.c_void_p),
     ]
 
 
@@ -186,6 +187,8 @@ def _config(wl, keep: _Keep, w_begin=0, w_end=None, n_threads=None, hash_=True,
     cfg.n_threads = n_threads or os.cpu_count() or 1
     cfg.hash = 1 if hash_ else 0
     cfg.interaction = int(getattr(wl, "interaction", 0))
+    rho = getattr(wl, "rho", None)
+    cfg.rho = None if rho is None else keep(rho, np.float64).ctypes.data
     return cfg
 
 

@@ -19,6 +19,9 @@
  *   - Sec. 2.1.4, Eq. 5: the weight alpha = exp(-sum_i t_i / T^(i)).
  *   - Sec. 2.3, Eq. 7: phase phi = int g(t).x(t) dt, S = <alpha e^{-i phi}>/<alpha>.
  *   - Sec. 2.3 (narrow-pulse D and K): alpha-weighted displacement moments.
+ *   - Sec. 2.1.3 (magnetization transfer): a walker meeting a membrane of
+ *     surface relaxivity rho is saturated with probability
+ *     P_MT = rho ds C_3 / D0 and contributes nothing afterwards (alpha_rho = 0).
  *   - Sec. 2.1.2, App. A and B: two alternative particle-membrane interactions
  *     the paper analyses for their bias.  Rejection sampling cancels a step
  *     that a membrane refuses (the walker stays, the step's dt still counts
@@ -40,7 +43,7 @@
  * "Parallel random numbers: as easy as 1, 2, 3"), written here from that
  * definition.  Counter layout: key = (seed_lo, seed_hi);
  * ctr = (walker_lo, walker_hi, step, tag << 16 | call), tag INIT=1, DIR=2,
- * PERM=3.  Trajectory checksum: SplitMix64 finaliser (Steele, Lea & Flood,
+ * PERM=3, MT=4.  Trajectory checksum: SplitMix64 finaliser (Steele, Lea & Flood,
  * OOPSLA'14).
  */
 #include <math.h>
@@ -52,6 +55,7 @@
 #define TAG_INIT 1u
 #define TAG_DIR 2u
 #define TAG_PERM 3u
+#define TAG_MT 4u
 
 /* error bits reported through rmso_run's return value */
 #define RMSO_ERR_BAD_ARG 4
@@ -139,6 +143,8 @@ typedef struct {
     int32_t hash;             /* 1: keep the trajectory checksum */
     int32_t interaction;      /* 0 elastic collision (Sec. 2.1.2-2.1.3), 1 rejection sampling
                                  (App. B), 2 equal-step-length random leap (App. A) */
+    const double *rho;        /* n_labels x n_labels surface relaxivity (um/ms) of the membrane met
+                                 from label r (row) towards label c (column), or NULL: none */
 } rmso_config;
 
 #define RMSO_EC 0
@@ -170,6 +176,7 @@ typedef struct {
     double *s;        /* ds_c / l_p : step length of label c in voxel units */
     double *dtR[3];   /* dt / T2_c, dt / T1_c, 0 : relaxation per unit time fraction */
     uint32_t *T;      /* per ordered pair: floor(P_{c->c'} 2^32), clamped */
+    uint32_t *Tmt;    /* per ordered pair: floor(P_MT 2^32), clamped (NULL: no absorbing membrane) */
     int64_t n_ok;
     int64_t *ok_list; /* raster list of non-dead voxels (NULL if none dead) */
     int any_relax;
@@ -190,6 +197,16 @@ double rmso_perm_prob(double kappa, double D1, double ds1, double D2, double ds2
     double num = ((kappa * ds1) / D1) * C;
     double den = 1.0 + ((kappa / 2.0) * ((ds1 / D1) + (ds2 / D2))) * C;
     return num / den;
+}
+
+/* Sec. 2.1.3 (magnetization transfer): the probability that a walker of
+ * label 1 (D1, ds1) meeting a membrane of surface relaxivity rho is
+ * saturated, P_MT = (rho ds1 / D1) C with C_3 = 2/3.  Evaluation order fixed:
+ * ((rho*ds1)/D1)*C. */
+double rmso_mt_prob(double rho, double D1, double ds1)
+{
+    const double C = 2.0 / 3.0;
+    return ((rho * ds1) / D1) * C;
 }
 
 /* Bernoulli threshold: cross iff a uniform 32-bit word e < T, with
@@ -238,6 +255,19 @@ static int build_ctx(const rmso_config *cfg, ctx *X)
             }
             X->T[(size_t)a * L + b] = rmso_threshold(rmso_perm_prob(k, cfg->D[a], ds[a], cfg->D[b], ds[b]));
         }
+    if (cfg->rho) {
+        X->Tmt = (uint32_t *)calloc((size_t)L * L, sizeof(uint32_t));
+        if (!X->Tmt) {
+            free(ds);
+            return RMSO_ERR_OOM;
+        }
+        for (int a = 0; a < L; a++)
+            for (int b = 0; b < L; b++) {
+                double r = cfg->rho[(size_t)a * L + b];
+                if (a == b || cfg->dead[a] || !(r > 0.0)) continue; /* a membrane into a dead label counts */
+                X->Tmt[(size_t)a * L + b] = rmso_threshold(rmso_mt_prob(r, cfg->D[a], ds[a]));
+            }
+    }
     free(ds);
     /* Sec. 2.2 item 1: uniform over non-dead voxels, raster order (x fastest) */
     int64_t nvox = (int64_t)cfg->nx * cfg->ny * cfg->nz;
@@ -262,6 +292,7 @@ static void free_ctx(ctx *X)
     free(X->s);
     for (int m = 0; m < 3; m++) free(X->dtR[m]);
     free(X->T);
+    free(X->Tmt);
     free(X->ok_list);
 }
 
@@ -506,6 +537,18 @@ static int walk_step(const ctx *X, uint64_t w, uint32_t k, walker *s, double n[3
             q[best] = j;
             c2 = label_at(cfg, q[0], q[1], q[2]);
         }
+        /* Sec. 2.1.3, magnetization transfer: meeting an absorbing membrane
+         * saturates the walker with probability P_MT (word e of the step's
+         * MT call, call = the attempt); a saturated walker's weight is 0 for
+         * good (Eq. wt-mt), kept as an infinite exponent A. */
+        if (X->Tmt && c2 >= 0 && c2 != s->c) {
+            uint32_t Tm = X->Tmt[(size_t)s->c * L + c2];
+            if (Tm != 0u && !isinf(s->A)) {
+                uint32_t m4[4];
+                draw(cfg->seed, w, k, TAG_MT, attempt, m4);
+                if (m4[ev] < Tm) s->A = INFINITY;
+            }
+        }
         int cross;
         if (c2 == s->c) {
             cross = 1;
@@ -635,18 +678,21 @@ static void *run_range(void *arg)
                  * direction (DIR call = attempt) until one is admitted. */
                 const walker s0 = s;
                 const double rate0 = X->dtR[mode][s.c];
-                int accepted = 0;
+                int accepted = 0, saturated = 0;
                 const uint32_t attempts = cfg->interaction == RMSO_ERL ? RMSO_MAX_LEAPS : 1u;
                 for (uint32_t att = 0; att < attempts && !accepted; att++) {
                     if (att > 0) {
-                        s = s0;
+                        s = s0; /* a saturation met on a cancelled draw stays */
+                        if (saturated) s.A = INFINITY;
                         direction_call(cfg->seed, (uint64_t)w, (uint32_t)k, att, n, perm01);
                     }
                     accepted = walk_step(X, (uint64_t)w, (uint32_t)k, &s, n, perm01, NULL, mode,
                                          cfg->interaction, att) == 0;
+                    saturated |= isinf(s.A);
                 }
                 if (!accepted) {
                     s = s0; /* stays for the step, in its label */
+                    if (saturated) s.A = INFINITY;
                     s.A = s.A + 1.0 * rate0;
                     s.n_refl++;
                     if (cfg->interaction == RMSO_ERL) J->err |= RMSO_ERR_LEAPS;

@@ -48,6 +48,8 @@ class Workload:
     n_walkers, seed
     interaction 0 elastic collision, 1 rejection sampling, 2 equal-step-length
                random leap (the particle-membrane interaction of a run)
+    rho        float64 (L, L) surface relaxivity (um/ms) of the membrane met from
+               label r towards label c (magnetization transfer), or None
     """
     name: str
     labels: np.ndarray
@@ -68,6 +70,7 @@ class Workload:
     n_walkers: int
     seed: int
     interaction: int = 0
+    rho: Optional[np.ndarray] = None
 
     @property
     def n_labels(self) -> int:
