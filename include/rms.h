@@ -109,13 +109,19 @@ typedef struct {
     const double *kappa;      /* host, L*L or NULL: permeability (um/ms) of the membrane from
                                  label r (row) into label c (column); diagonal ignored */
     double kappa_scalar;      /* used for every pair when kappa == NULL */
+    const double *rho;        /* host, L*L or NULL: surface relaxivity (um/ms) of the membrane met
+                                 from label r (row) towards label c (column), for magnetization
+                                 transfer (Sec. 2.1.3): each such face event saturates the walker
+                                 with probability P_MT = (rho ds_r / D_r) C_3 (C_3 = 2/3; clamped to
+                                 1 with RMS_W_PROB_RANGE), after which its weight is 0.  A membrane
+                                 into a dead label counts; diagonal ignored; NULL: none */
     const uint8_t *dead;      /* host, L or NULL: 1 = no walker starts in or enters the label */
     void *stream;             /* cudaStream_t for the upload */
 } rms_substrate_desc;
 
 /* Upload the volume and build the per-label tables.  Errors:
- * RMS_E_INVALID_ARG, RMS_E_OOM, RMS_E_CUDA.  The permeation thresholds are
- * built when a sequence fixes dt (rms_set_sequence). */
+ * RMS_E_INVALID_ARG, RMS_E_OOM, RMS_E_CUDA.  The permeation and saturation
+ * thresholds are built when a sequence fixes dt (rms_set_sequence). */
 rms_status rms_create_substrate(const rms_substrate_desc *desc, rms_substrate **out);
 
 /* Free the substrate.  RMS_E_BUSY (and nothing freed) while a sequence made
@@ -201,7 +207,8 @@ rms_status rms_read_signal(rms_run_handle *run, double *S_re, double *S_im, doub
                            double *alpha_sum);
 
 /* Wait for the run and copy the final per-walker state to host memory (any
- * pointer may be NULL; return codes as rms_read_signal): i (W*3 int32 unwrapped voxel index), o (W*3 double
+ * pointer may be NULL; return codes as rms_read_signal; a saturated walker's
+ * A is +INFINITY): i (W*3 int32 unwrapped voxel index), o (W*3 double
  * offset in [0,1]; the FP32 form's offsets widened), i0 (W*3), o0 (W*3),
  * c (W int32 label), A (W double exponent of Eq. 5), phase (W*n_shapes*3
  * double, sum_k dt G_k dx_k in um ms), hash (W uint64, RMS_TRAJ_HASH runs). */
@@ -237,8 +244,9 @@ rms_status rms_server_create(const rms_server_config *cfg, rms_server **out);
 /* Queue a request: n_walkers walkers of `seq` (its substrate stays resident;
  * both must outlive the request -- destroying them returns RMS_E_BUSY
  * meanwhile), Philox key `seed`, RMS_FP64 or RMS_FP32, elastic collision
- * (RMS_EC).  Returns at once with a ticket.  The result equals rms_run's for
- * the same arguments. */
+ * (RMS_EC), on a substrate without absorbing membranes (rho == NULL, else
+ * RMS_E_INVALID_ARG).  Returns at once with a ticket.  The result equals
+ * rms_run's for the same arguments. */
 rms_status rms_server_submit(rms_server *srv, rms_sequence *seq, int64_t n_walkers, uint64_t seed,
                              int32_t precision, int64_t *ticket);
 

@@ -42,7 +42,7 @@ class SubstrateDesc(C.Structure):
                 ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("voxel_um", C.c_double), ("periodic", C.c_int32 * 3), ("n_labels", C.c_int32),
                 ("D", C.c_void_p), ("T2", C.c_void_p), ("T1", C.c_void_p), ("kappa", C.c_void_p),
-                ("kappa_scalar", C.c_double), ("dead", C.c_void_p), ("stream", C.c_void_p)]
+                ("kappa_scalar", C.c_double), ("rho", C.c_void_p), ("dead", C.c_void_p), ("stream", C.c_void_p)]
 
 
 class SequenceDesc(C.Structure):

@@ -166,6 +166,33 @@ __global__ void pair_tables_kernel(int32_t L, const double *D, const double *kap
     T[idx] = thr;
 }
 
+// Sec. 2.1.3 (magnetization transfer): saturation thresholds
+// T_mt = floor(P_MT 2^32) for a walker of label a meeting an absorbing
+// membrane towards label b, P_MT = (rho ds_a / D_a) C_3.  A membrane into a
+// dead label counts; none inside a label.
+__global__ void mt_tables_kernel(int32_t L, const double *D, const double *rho, const uint8_t *dead, double dt,
+                                 uint32_t *Tmt, int32_t *warn)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)L * L) return;
+    const int a = (int)(idx / L), b = (int)(idx % L);
+    const double r = rho[idx];
+    uint32_t thr = 0u;
+    if (a != b && !dead[a] && r > 0.0) {
+        const double C = 2.0 / 3.0;
+        const double ds1 = sqrt((6.0 * D[a]) * dt);
+        const double P = ((r * ds1) / D[a]) * C;
+        if (P > 1.0) atomicOr(warn, 1);
+        if (P >= 1.0) {
+            thr = 0xFFFFFFFFu;
+        } else if (P > 0.0) {
+            const double x = floor(P * 4294967296.0);
+            thr = x >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)x;
+        }
+    }
+    Tmt[idx] = thr;
+}
+
 // The azimuth table: (cos, sin) of the centres (2j + 1) 2^-11 pi/4 of the
 // 1024 parts of [0, pi/4].
 __global__ void trig_table_kernel(double *trig)
@@ -388,7 +415,10 @@ __global__ void export_kernel(WalkerState<Real> st, int64_t W, int32_t S, bool h
         o0[3 * w + a] = (double)st.o0[a][w];
     }
     c[w] = st.c[w];
-    A[w] = st.A_c ? (double)st.A[w] - (double)st.A_c[w] : (double)st.A[w];
+    if (st.A_c)  // FP32 form: Kahan sum; kSaturatedF marks a saturated walker
+        A[w] = (float)st.A[w] >= kSaturatedF ? (double)INFINITY : (double)st.A[w] - (double)st.A_c[w];
+    else
+        A[w] = (double)st.A[w];
     for (int k = 0; k < S * 3; ++k) {
         double p = (double)st.phase[(int64_t)k * W + w];
         if (st.phase_c) p = p - (double)st.phase_c[(int64_t)k * W + w];
@@ -417,6 +447,7 @@ static void free_substrate(rms_substrate *s, cudaStream_t st)
     cudaFreeAsync(s->d_T2, st);
     cudaFreeAsync(s->d_T1, st);
     cudaFreeAsync(s->d_kappa, st);
+    if (s->d_rho) cudaFreeAsync(s->d_rho, st);
     cudaFreeAsync(s->d_dead, st);
     if (s->d_ok) cudaFreeAsync(s->d_ok, st);
 }
@@ -441,6 +472,7 @@ static rms_status create_substrate_impl(const rms_substrate_desc *d, rms_substra
         s->kappa.assign(d->kappa, d->kappa + (size_t)L * L);
     else
         s->kappa.assign((size_t)L * L, d->kappa_scalar);
+    if (d->rho) s->rho.assign(d->rho, d->rho + (size_t)L * L);
     s->dead.assign(L, 0);
     if (d->dead)
         for (int c = 0; c < L; ++c) s->dead[c] = d->dead[c] ? 1 : 0;
@@ -453,11 +485,15 @@ static rms_status create_substrate_impl(const rms_substrate_desc *d, rms_substra
     for (size_t k = 0; k < s->kappa.size(); ++k)
         if (!(s->kappa[k] >= 0.0) || !std::isfinite(s->kappa[k]))
             return fail(RMS_E_INVALID_ARG, "kappa must be finite and >= 0");
+    for (size_t k = 0; k < s->rho.size(); ++k)
+        if (!(s->rho[k] >= 0.0) || !std::isfinite(s->rho[k]))
+            return fail(RMS_E_INVALID_ARG, "rho must be finite and >= 0");
     RMS_TRY(upload(&s->d_labels, d->labels, (size_t)nvox, st, d->labels_on_device != 0));
     RMS_TRY(upload(&s->d_D, s->D.data(), L, st));
     RMS_TRY(upload(&s->d_T2, s->T2.data(), L, st));
     RMS_TRY(upload(&s->d_T1, s->T1.data(), L, st));
     RMS_TRY(upload(&s->d_kappa, s->kappa.data(), (size_t)L * L, st));
+    if (!s->rho.empty()) RMS_TRY(upload(&s->d_rho, s->rho.data(), (size_t)L * L, st));
     RMS_TRY(upload(&s->d_dead, s->dead.data(), L, st));
     // every label must be < L
     uint32_t *d_max = nullptr;
@@ -538,8 +574,8 @@ extern "C" rms_status rms_destroy_substrate(rms_substrate *s)
 
 static void free_sequence(rms_sequence *q, cudaStream_t st)
 {
-    void *p[] = {q->d_s64, q->d_dtR64, q->d_wG64, q->d_s32, q->d_dtR32, q->d_wG32, q->d_T, q->d_flags,
-                 q->d_mode, q->d_rec_of, q->d_dirs, q->d_b, q->d_bs, q->d_q, q->d_trig};
+    void *p[] = {q->d_s64, q->d_dtR64, q->d_wG64, q->d_s32, q->d_dtR32, q->d_wG32, q->d_T, q->d_Tmt,
+                 q->d_flags, q->d_mode, q->d_rec_of, q->d_dirs, q->d_b, q->d_bs, q->d_q, q->d_trig};
     for (void *x : p)
         if (x) cudaFreeAsync(x, st);
 }
@@ -578,6 +614,7 @@ static rms_status set_sequence_impl(rms_substrate *sub, const rms_sequence_desc 
     RMS_CUDA(cudaMallocAsync((void **)&q->d_dtR64, sizeof(double) * 3 * L, st));
     RMS_CUDA(cudaMallocAsync((void **)&q->d_dtR32, sizeof(float) * 3 * L, st));
     RMS_CUDA(cudaMallocAsync((void **)&q->d_T, sizeof(uint32_t) * (size_t)L * L, st));
+    if (sub->d_rho) RMS_CUDA(cudaMallocAsync((void **)&q->d_Tmt, sizeof(uint32_t) * (size_t)L * L, st));
     const size_t nG = (size_t)S * (N ? N : 1);
     RMS_CUDA(cudaMallocAsync((void **)&q->d_wG64, sizeof(double) * nG, st));
     RMS_CUDA(cudaMallocAsync((void **)&q->d_wG32, sizeof(float) * nG, st));
@@ -605,6 +642,9 @@ static rms_status set_sequence_impl(rms_substrate *sub, const rms_sequence_desc 
     const int64_t LL = (int64_t)L * L;
     pair_tables_kernel<<<(unsigned)((LL + 255) / 256), 256, 0, st>>>(L, sub->d_D, sub->d_kappa, sub->d_dead,
                                                                       d->dt_ms, q->d_T, d_warn);
+    if (sub->d_rho)
+        mt_tables_kernel<<<(unsigned)((LL + 255) / 256), 256, 0, st>>>(L, sub->d_D, sub->d_rho, sub->d_dead,
+                                                                        d->dt_ms, q->d_Tmt, d_warn);
     if (N > 0)
         step_tables_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, S, d->dt_ms, d_G, d_rec, d->n_rec,
                                                                          q->d_wG64, q->d_wG32, q->d_flags,
@@ -704,12 +744,12 @@ ReqDesc<Real> rms::run_desc(rms_run_handle *r)
     d.g = Geometry{sub->d_labels, sub->nx, sub->ny, sub->nz, sub->periodic[0], sub->periodic[1], sub->periodic[2],
                    sub->voxel_um};
     if constexpr (std::is_same<Real, float>::value) {
-        d.t = Tables<float>{q->d_s32, q->d_dtR32, q->d_T, sub->L, q->d_wG32, q->d_flags, q->d_rec_of, q->d_mode,
-                            q->any_relax, q->d_trig};
+        d.t = Tables<float>{q->d_s32, q->d_dtR32, q->d_T, q->d_Tmt, sub->L, q->d_wG32, q->d_flags, q->d_rec_of,
+                            q->d_mode, q->any_relax, q->d_trig};
         d.st = r->st32;
     } else {
-        d.t = Tables<double>{q->d_s64, q->d_dtR64, q->d_T, sub->L, q->d_wG64, q->d_flags, q->d_rec_of, q->d_mode,
-                             q->any_relax, q->d_trig};
+        d.t = Tables<double>{q->d_s64, q->d_dtR64, q->d_T, q->d_Tmt, sub->L, q->d_wG64, q->d_flags, q->d_rec_of,
+                             q->d_mode, q->any_relax, q->d_trig};
         d.st = r->st64;
     }
     d.ctl.seed = r->seed;
@@ -750,16 +790,20 @@ static rms_status walk_impl(rms_run_handle *r, int64_t k0, int64_t k1)
     const bool hash = (r->flags & RMS_TRAJ_HASH) != 0;
     const dim3 grid((unsigned)r->n_blocks);
     const int S = r->seq->S;
+#define RMS_WALK(IM, MT) \
+    RMS_CUDA((launch_walk<Real, IM, MT>(S, hash, grid, r->stream, d.g, d.t, d.st, d.ctl, k0, k1)))
+    const bool mt = d.t.Tmt != nullptr;
     switch (r->interaction) {
     case RMS_RS:
-        RMS_CUDA((launch_walk<Real, kInteractRS>(S, hash, grid, r->stream, d.g, d.t, d.st, d.ctl, k0, k1)));
+        if (mt) RMS_WALK(kInteractRS, true); else RMS_WALK(kInteractRS, false);
         break;
     case RMS_ERL:
-        RMS_CUDA((launch_walk<Real, kInteractERL>(S, hash, grid, r->stream, d.g, d.t, d.st, d.ctl, k0, k1)));
+        if (mt) RMS_WALK(kInteractERL, true); else RMS_WALK(kInteractERL, false);
         break;
     default:
-        RMS_CUDA((launch_walk<Real, kInteractEC>(S, hash, grid, r->stream, d.g, d.t, d.st, d.ctl, k0, k1)));
+        if (mt) RMS_WALK(kInteractEC, true); else RMS_WALK(kInteractEC, false);
     }
+#undef RMS_WALK
     return RMS_OK;
 }
 

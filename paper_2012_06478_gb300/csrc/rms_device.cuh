@@ -32,7 +32,7 @@ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1)
 
 // Counter layout: key (seed_lo, seed_hi); counter (walker_lo, walker_hi,
 // step, tag << 16 | call).
-enum : uint32_t { kTagInit = 1u, kTagDir = 2u, kTagPerm = 3u };
+enum : uint32_t { kTagInit = 1u, kTagDir = 2u, kTagPerm = 3u, kTagMT = 4u };
 
 __device__ __forceinline__ U4 draw(uint64_t seed, uint64_t w, uint32_t step, uint32_t tag,
                                    uint32_t call)
@@ -86,6 +86,12 @@ constexpr int kMaxShapes = 8;
 // admissible direction in kMaxLeaps draws; the walker stayed for that step).
 enum : int { kErrTimeout = 4, kWarnLeaps = 8 };
 
+// A saturated walker (Sec. 2.1.3, magnetization transfer) has weight 0 for
+// good.  The FP64 form keeps A = +inf, as the CPU reference does; the FP32
+// form keeps A = kSaturatedF (its Kahan sum would turn +inf into NaN), which
+// the walker export turns into +inf.
+constexpr float kSaturatedF = 1e30f;
+
 // Particle-membrane interaction (Sec. 2.1.2, App. A and B).
 enum : int { kInteractEC = 0, kInteractRS = 1, kInteractERL = 2 };
 constexpr uint32_t kMaxLeaps = 64;  // ERL draws per step
@@ -117,6 +123,7 @@ struct Tables {
     const Real *s;          // step length per label, voxel units
     const Real *dtR;        // [mode][label]: dt / T (0 = none)
     const uint32_t *T;      // [from][to] Bernoulli thresholds
+    const uint32_t *Tmt;    // [from][to] saturation thresholds (MT), or nullptr
     int32_t n_labels;
     const Real *wG;         // [shape][step]: dt * G
     const uint8_t *flags;   // [step]: bit0 any G != 0, bit1 recording step

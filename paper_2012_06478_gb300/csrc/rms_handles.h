@@ -18,9 +18,10 @@ struct rms_substrate {
     int32_t periodic[3] = {1, 1, 1};
     int32_t L = 0;
     std::vector<double> D, T2, T1, kappa;
+    std::vector<double> rho;  // surface relaxivity per pair (empty: no absorbing membrane)
     std::vector<uint8_t> dead;
     uint16_t *d_labels = nullptr;
-    double *d_D = nullptr, *d_T2 = nullptr, *d_T1 = nullptr, *d_kappa = nullptr;
+    double *d_D = nullptr, *d_T2 = nullptr, *d_T1 = nullptr, *d_kappa = nullptr, *d_rho = nullptr;
     uint8_t *d_dead = nullptr;
     int32_t *d_ok = nullptr;  // raster list of non-dead voxels (nullptr: none dead)
     int64_t n_ok = 0;
@@ -37,6 +38,7 @@ struct rms_sequence {
     double *d_s64 = nullptr, *d_dtR64 = nullptr, *d_wG64 = nullptr;
     float *d_s32 = nullptr, *d_dtR32 = nullptr, *d_wG32 = nullptr;
     uint32_t *d_T = nullptr;
+    uint32_t *d_Tmt = nullptr;  // saturation thresholds (nullptr: no absorbing membrane)
     uint8_t *d_flags = nullptr, *d_mode = nullptr;
     int32_t *d_rec_of = nullptr;
     double *d_dirs = nullptr, *d_b = nullptr, *d_bs = nullptr, *d_q = nullptr;

@@ -7,21 +7,27 @@
 
 namespace rms {
 
-template <typename Real, int IM>
+template <typename Real, int IM, bool MT>
 cudaError_t launch_walk(int n_shapes, bool hash, dim3 grid, cudaStream_t stream, const Geometry &g,
                         const Tables<Real> &t, const WalkerState<Real> &st, const RunCtl &ctl,
                         int64_t k_begin, int64_t k_end);
 
-#define RMS_EXTERN_LAUNCH_WALK(REAL, IM)                                                                   \
-    extern template cudaError_t launch_walk<REAL, IM>(int, bool, dim3, cudaStream_t, const Geometry &,    \
-                                                      const Tables<REAL> &, const WalkerState<REAL> &,    \
-                                                      const RunCtl &, int64_t, int64_t);
-RMS_EXTERN_LAUNCH_WALK(double, kInteractEC)
-RMS_EXTERN_LAUNCH_WALK(double, kInteractRS)
-RMS_EXTERN_LAUNCH_WALK(double, kInteractERL)
-RMS_EXTERN_LAUNCH_WALK(float, kInteractEC)
-RMS_EXTERN_LAUNCH_WALK(float, kInteractRS)
-RMS_EXTERN_LAUNCH_WALK(float, kInteractERL)
+#define RMS_EXTERN_LAUNCH_WALK(REAL, IM, MT)                                                               \
+    extern template cudaError_t launch_walk<REAL, IM, MT>(int, bool, dim3, cudaStream_t, const Geometry &, \
+                                                          const Tables<REAL> &, const WalkerState<REAL> &, \
+                                                          const RunCtl &, int64_t, int64_t);
+RMS_EXTERN_LAUNCH_WALK(double, kInteractEC, false)
+RMS_EXTERN_LAUNCH_WALK(double, kInteractRS, false)
+RMS_EXTERN_LAUNCH_WALK(double, kInteractERL, false)
+RMS_EXTERN_LAUNCH_WALK(float, kInteractEC, false)
+RMS_EXTERN_LAUNCH_WALK(float, kInteractRS, false)
+RMS_EXTERN_LAUNCH_WALK(float, kInteractERL, false)
+RMS_EXTERN_LAUNCH_WALK(double, kInteractEC, true)
+RMS_EXTERN_LAUNCH_WALK(double, kInteractRS, true)
+RMS_EXTERN_LAUNCH_WALK(double, kInteractERL, true)
+RMS_EXTERN_LAUNCH_WALK(float, kInteractEC, true)
+RMS_EXTERN_LAUNCH_WALK(float, kInteractRS, true)
+RMS_EXTERN_LAUNCH_WALK(float, kInteractERL, true)
 #undef RMS_EXTERN_LAUNCH_WALK
 
 template <typename Real>

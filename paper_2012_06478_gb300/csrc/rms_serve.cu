@@ -474,6 +474,7 @@ extern "C" rms_status rms_server_submit(rms_server *s, rms_sequence *seq, int64_
     if (!s || !seq || !ticket) return fail(RMS_E_INVALID_ARG, "null argument");
     if (n_walkers < 1 || n_walkers > (1ll << 31) - 1) return fail(RMS_E_INVALID_ARG, "n_walkers out of range");
     if (precision != RMS_FP32 && precision != RMS_FP64) return fail(RMS_E_INVALID_ARG, "precision");
+    if (seq->d_Tmt) return fail(RMS_E_INVALID_ARG, "served requests have no absorbing membranes (rho); use rms_run");
     Request *q = new (std::nothrow) Request();
     if (!q) return fail(RMS_E_OOM, "host allocation");
     q->seq = seq;

@@ -5,7 +5,7 @@
 #include "rms_internal.h"
 
 namespace rms {
-template cudaError_t launch_walk<float, kInteractEC>(int, bool, dim3, cudaStream_t, const Geometry &,
+template cudaError_t launch_walk<float, kInteractEC, false>(int, bool, dim3, cudaStream_t, const Geometry &,
                                         const Tables<float> &, const WalkerState<float> &,
                                         const RunCtl &, int64_t, int64_t);
 template cudaError_t launch_walk_batched<float>(int, int32_t, cudaStream_t, const ReqDesc<float> *,

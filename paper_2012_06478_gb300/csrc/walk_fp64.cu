@@ -5,7 +5,7 @@
 #include "rms_internal.h"
 
 namespace rms {
-template cudaError_t launch_walk<double, kInteractEC>(int, bool, dim3, cudaStream_t, const Geometry &,
+template cudaError_t launch_walk<double, kInteractEC, false>(int, bool, dim3, cudaStream_t, const Geometry &,
                                          const Tables<double> &, const WalkerState<double> &,
                                          const RunCtl &, int64_t, int64_t);
 template cudaError_t launch_walk_batched<double>(int, int32_t, cudaStream_t, const ReqDesc<double> *,

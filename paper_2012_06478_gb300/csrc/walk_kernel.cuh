@@ -121,6 +121,16 @@ __device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, const d
     n[2] = z;
 }
 
+// Saturation (Sec. 2.1.3): A = +inf (FP64 form) or kSaturatedF (FP32 form).
+__device__ __forceinline__ bool saturated(double A) { return dbits(A) == 0x7FF0000000000000LL; }
+__device__ __forceinline__ bool saturated(float A) { return A >= kSaturatedF; }
+__device__ __forceinline__ void saturate(double &A, double &) { A = __longlong_as_double(0x7FF0000000000000LL); }
+__device__ __forceinline__ void saturate(float &A, float &Ac)
+{
+    A = kSaturatedF;
+    Ac = 0.0f;
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -176,8 +186,9 @@ __device__ __forceinline__ void warp_moments(double al, const double dx[3], doub
 // paper's method), or one of the alternatives of App. A and B, in which a
 // refused face cancels the step -- rejection sampling keeps the walker where
 // it was for the step, ERL draws a new direction (DIR and PERM call = the
-// draw's index) until a step is admitted, at most kMaxLeaps draws.
-template <typename Real, int NS, bool HASH, int IM>
+// draw's index) until a step is admitted, at most kMaxLeaps draws.  MT adds
+// absorbing membranes (Sec. 2.1.3, magnetization transfer; t.Tmt non-null).
+template <typename Real, int NS, bool HASH, int IM, bool MT>
 __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real> &t, const WalkerState<Real> &st,
                                            const RunCtl &ctl, int64_t block, int64_t k_begin, int64_t k_end)
 {
@@ -257,6 +268,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                 Ac_s = Ac;
             }
             uint32_t att = 0;  // draw index (ERL redraws); always 0 otherwise
+            [[maybe_unused]] bool sat_any = false;  // saturated on some draw of this step (MT)
 #pragma unroll 1
             for (;;) {
             // ---- direction (one DIR call: words 0, 1 -> direction; words 2, 3 ->
@@ -302,6 +314,18 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                     }
                 }
                 const int32_t c2 = wall ? -1 : (int32_t)__ldg(g.labels + nv);
+                // magnetization transfer (Sec. 2.1.3): meeting an absorbing membrane
+                // saturates the walker with probability P_MT -- word `ev` of the
+                // step's MT call (call = the draw index)
+                if constexpr (MT) {
+                    if (c2 >= 0 && c2 != c) {
+                        const uint32_t tm = __ldg(t.Tmt + (int64_t)c * L + c2);
+                        if (tm != 0u && !saturated(A)) {
+                            const U4 m = draw(ctl.seed, w, (uint32_t)k, kTagMT, att);
+                            if ((ev == 0 ? m.x : (ev == 1 ? m.y : m.z)) < tm) saturate(A, Ac);
+                        }
+                    }
+                }
                 bool cross;
                 if (c2 == c) {
                     cross = true;
@@ -482,6 +506,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                 break;
             } else {
                 if (!refused) break;
+                if constexpr (MT) sat_any = sat_any || saturated(A);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     o[a] = o_s[a];
@@ -492,6 +517,9 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                 c = c_s;
                 A = A_s;
                 Ac = Ac_s;
+                if constexpr (MT) {
+                    if (sat_any) saturate(A, Ac);  // a saturation met on a cancelled draw stays
+                }
                 if (IM == kInteractRS || ++att >= kMaxLeaps) {
                     // the walker stays for the step, in its label
                     if (t.any_relax) {
@@ -576,11 +604,11 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
 }
 
 // One run: block b of the grid advances walkers b*kWalkBlock ... of the run.
-template <typename Real, int NS, bool HASH, int IM>
+template <typename Real, int NS, bool HASH, int IM, bool MT>
 __global__ void __launch_bounds__(kWalkBlock)
 walk_kernel(Geometry g, Tables<Real> t, WalkerState<Real> st, RunCtl ctl, int64_t k_begin, int64_t k_end)
 {
-    walk_block<Real, NS, HASH, IM>(g, t, st, ctl, blockIdx.x, k_begin, k_end);
+    walk_block<Real, NS, HASH, IM, MT>(g, t, st, ctl, blockIdx.x, k_begin, k_end);
 }
 
 // Many runs in one launch (continuous batching): block i executes task i --
@@ -598,8 +626,8 @@ walk_batched_kernel(const ReqDesc<Real> *reqs, const BlockTask *tasks, int32_t n
         s_req = reqs[s_task.req];
     }
     __syncthreads();
-    walk_block<Real, NS, false, kInteractEC>(s_req.g, s_req.t, s_req.st, s_req.ctl, s_task.block, s_task.k0,
-                                             s_task.k1);
+    walk_block<Real, NS, false, kInteractEC, false>(s_req.g, s_req.t, s_req.st, s_req.ctl, s_task.block,
+                                                    s_task.k0, s_task.k1);
 }
 
 template <typename Real>
@@ -619,10 +647,11 @@ cudaError_t launch_walk_batched(int ns_bucket, int32_t n_tasks, cudaStream_t str
     return cudaGetLastError();
 }
 
-// Host-side launcher for interaction IM, instantiated in walk_fp64.cu /
-// walk_fp32.cu (elastic collision) and walk_reject_fp64.cu /
-// walk_reject_fp32.cu (rejection sampling, ERL).
-template <typename Real, int IM>
+// Host-side launcher for interaction IM and absorbing membranes MT,
+// instantiated in walk_fp64.cu / walk_fp32.cu (elastic collision),
+// walk_reject_fp64.cu / walk_reject_fp32.cu (rejection sampling, ERL) and
+// walk_mt_fp64.cu / walk_mt_fp32.cu (the three with absorbing membranes).
+template <typename Real, int IM, bool MT>
 cudaError_t launch_walk(int n_shapes, bool hash, dim3 grid, cudaStream_t stream, const Geometry &g,
                         const Tables<Real> &t, const WalkerState<Real> &st, const RunCtl &ctl,
                         int64_t k_begin, int64_t k_end)
@@ -630,11 +659,11 @@ cudaError_t launch_walk(int n_shapes, bool hash, dim3 grid, cudaStream_t stream,
 #define RMS_LAUNCH(NSV)                                                                              \
     do {                                                                                             \
         if (hash)                                                                                    \
-            walk_kernel<Real, NSV, true, IM><<<grid, kWalkBlock, 0, stream>>>(g, t, st, ctl, k_begin, \
-                                                                             k_end);                 \
+            walk_kernel<Real, NSV, true, IM, MT><<<grid, kWalkBlock, 0, stream>>>(g, t, st, ctl,     \
+                                                                                 k_begin, k_end);    \
         else                                                                                         \
-            walk_kernel<Real, NSV, false, IM><<<grid, kWalkBlock, 0, stream>>>(g, t, st, ctl,        \
-                                                                              k_begin, k_end);       \
+            walk_kernel<Real, NSV, false, IM, MT><<<grid, kWalkBlock, 0, stream>>>(g, t, st, ctl,    \
+                                                                                  k_begin, k_end);   \
     } while (0)
     if (n_shapes <= 1)
         RMS_LAUNCH(1);

@@ -5,10 +5,10 @@
 #include "rms_internal.h"
 
 namespace rms {
-template cudaError_t launch_walk<float, kInteractRS>(int, bool, dim3, cudaStream_t, const Geometry &,
+template cudaError_t launch_walk<float, kInteractRS, false>(int, bool, dim3, cudaStream_t, const Geometry &,
                                                      const Tables<float> &, const WalkerState<float> &,
                                                      const RunCtl &, int64_t, int64_t);
-template cudaError_t launch_walk<float, kInteractERL>(int, bool, dim3, cudaStream_t, const Geometry &,
+template cudaError_t launch_walk<float, kInteractERL, false>(int, bool, dim3, cudaStream_t, const Geometry &,
                                                       const Tables<float> &, const WalkerState<float> &,
                                                       const RunCtl &, int64_t, int64_t);
 }  // namespace rms

@@ -7,10 +7,10 @@
 #include "rms_internal.h"
 
 namespace rms {
-template cudaError_t launch_walk<double, kInteractRS>(int, bool, dim3, cudaStream_t, const Geometry &,
+template cudaError_t launch_walk<double, kInteractRS, false>(int, bool, dim3, cudaStream_t, const Geometry &,
                                                       const Tables<double> &, const WalkerState<double> &,
                                                       const RunCtl &, int64_t, int64_t);
-template cudaError_t launch_walk<double, kInteractERL>(int, bool, dim3, cudaStream_t, const Geometry &,
+template cudaError_t launch_walk<double, kInteractERL, false>(int, bool, dim3, cudaStream_t, const Geometry &,
                                                        const Tables<double> &, const WalkerState<double> &,
                                                        const RunCtl &, int64_t, int64_t);
 }  // namespace rms

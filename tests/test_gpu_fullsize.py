@@ -7,7 +7,7 @@ match them bit for bit; the FP32 form is checked against the FP64 path's
 full-size signal and moments (|dS| <= 1e-3, D within 1 %, K within
 0.01 max(|K|, 0.1)), plus, for runs long enough that FP32 rounding drift
 decorrelates some walkers from their FP64 twins, 4.5 standard errors of the
-paired per-walker differences."""
+paired per-walker differences (weighted by alpha / <alpha>, as D and K are)."""
 import os
 
 import numpy as np
@@ -76,12 +76,16 @@ def _check_fp32(wl, g64, g32):
         x64 = wl.voxel_um * ((g64["i"] - g64["i0"]) + (g64["o"] - g64["o0"]))
         x32 = wl.voxel_um * ((g32["i"] - g32["i0"]) + (g32["o"] - g32["o0"]))
         W = x64.shape[0]
-        m2d = x32 ** 2 - x64 ** 2
+        # per-walker weights alpha / <alpha> (D and K are alpha-weighted)
+        a64, a32 = np.exp(-g64["A"]), np.exp(-g32["A"])
+        w64, w32 = (a64 / a64.mean())[:, None], (a32 / a32.mean())[:, None]
+        m2d = w32 * x32 ** 2 - w64 * x64 ** 2
         sD = m2d.std(axis=0) / np.sqrt(W) / (2 * t[-1])
         assert np.all(np.abs(D32[-1] - D64[-1]) <= 0.01 * D64[-1] + 4.5 * sD)
-        m4d = x32 ** 4 - x64 ** 4
-        m2 = (x64 ** 2).mean(axis=0)
-        sK = np.sqrt((m4d.std(axis=0) / m2 ** 2) ** 2 + (2 * (x64 ** 4).mean(0) / m2 ** 3 * m2d.std(axis=0)) ** 2)
+        m4d = w32 * x32 ** 4 - w64 * x64 ** 4
+        m2 = (w64 * x64 ** 2).mean(axis=0)
+        m4 = (w64 * x64 ** 4).mean(axis=0)
+        sK = np.sqrt((m4d.std(axis=0) / m2 ** 2) ** 2 + (2 * m4 / m2 ** 3 * m2d.std(axis=0)) ** 2)
         sK = sK / np.sqrt(W)
         assert np.all(np.abs(K32[-1] - K64[-1]) <= 0.01 * np.maximum(np.abs(K64[-1]), 0.1) + 4.5 * sK)
     else:
