@@ -59,7 +59,7 @@ class _Config(C.Structure):
         ("G", C.c_void_p), ("mode", C.c_void_p), ("n_rec", C.c_int32), ("rec_steps", C.c_void_p),
         ("seed", C.c_uint64), ("w_begin", C.c_int64), ("w_end", C.c_int64),
         ("n_threads", C.c_int32), ("hash", C.c_int32), ("interaction", C.c_int32),
-        ("rho", C.c_void_p),
+        ("rho", C.c_void_p), ("conc", C.c_void_p), ("lam", C.c_double), ("perm_model", C.c_int32),
     ]
 
 
@@ -189,6 +189,10 @@ def _config(wl, keep: _Keep, w_begin=0, w_end=None, n_threads=None, hash_=True,
     cfg.interaction = int(getattr(wl, "interaction", 0))
     rho = getattr(wl, "rho", None)
     cfg.rho = None if rho is None else keep(rho, np.float64).ctypes.data
+    conc = getattr(wl, "conc", None)
+    cfg.conc = None if conc is None else keep(conc, np.float64).ctypes.data
+    cfg.lam = float(getattr(wl, "lam", -1.0))
+    cfg.perm_model = int(getattr(wl, "perm_model", 0))
     return cfg
 
 

@@ -145,6 +145,12 @@ typedef struct {
                                  (App. B), 2 equal-step-length random leap (App. A) */
     const double *rho;        /* n_labels x n_labels surface relaxivity (um/ms) of the membrane met
                                  from label r (row) towards label c (column), or NULL: none */
+    /* App. C.2-C.3: spin concentration and the permeation model */
+    const double *conc;       /* per label spin concentration (> 0 where walkers live), or NULL: all 1 */
+    double lambda;            /* exponent of (c2/c1) in the generalised Eq. 3, in [0,1] (the label of
+                                 lower index is side 1); < 0: the lambda minimising alpha_lambda */
+    int32_t perm_model;       /* 0 nominal kappa (Eq. 3 generalised), 1 Baxter (kappa > 0 only marks
+                                 a permeable pair) */
 } rmso_config;
 
 #define RMSO_EC 0
@@ -152,6 +158,10 @@ typedef struct {
 #define RMSO_ERL 2
 #define RMSO_MAX_LEAPS 64
 #define RMSO_ERR_LEAPS 16 /* an ERL step found no admissible direction in RMSO_MAX_LEAPS draws */
+#define RMSO_PERM_KAPPA 0
+#define RMSO_PERM_BAXTER 1
+#define RMSO_MAX_INIT 256
+#define RMSO_ERR_INIT 32  /* a walker found no accepted start in RMSO_MAX_INIT draws */
 
 typedef struct {
     /* per walker, index = w - w_begin */
@@ -177,6 +187,7 @@ typedef struct {
     double *dtR[3];   /* dt / T2_c, dt / T1_c, 0 : relaxation per unit time fraction */
     uint32_t *T;      /* per ordered pair: floor(P_{c->c'} 2^32), clamped */
     uint32_t *Tmt;    /* per ordered pair: floor(P_MT 2^32), clamped (NULL: no absorbing membrane) */
+    uint64_t *acc;    /* per label: start accepted iff word < acc (density ~ conc); NULL: always */
     int64_t n_ok;
     int64_t *ok_list; /* raster list of non-dead voxels (NULL if none dead) */
     int any_relax;
@@ -197,6 +208,42 @@ double rmso_perm_prob(double kappa, double D1, double ds1, double D2, double ds2
     double num = ((kappa * ds1) / D1) * C;
     double den = 1.0 + ((kappa / 2.0) * ((ds1 / D1) + (ds2 / D2))) * C;
     return num / den;
+}
+
+/* App. C.2, the generalised Eq. 3 for spin concentrations c1 (side of the
+ * walker, D1, ds1) and c2: with f12 = (c2/c1)^lambda12 and
+ * f21 = (c1/c2)^lambda21, lambda21 = 1 - lambda12,
+ *   P = (kappa ds1 C f12 / D1) / (1 + (kappa/2)(ds1 f12/D1 + ds2 f21/D2) C),
+ * which keeps P12/P21 = c2 sqrt(D2) / (c1 sqrt(D1)) (equilibrium density ratio
+ * c1/c2) and applies the finite-step correction kappa = kappa0/(1 - alpha_lambda).
+ * Evaluation order fixed as written; f = 1 gives rmso_perm_prob's bits. */
+double rmso_perm_prob_conc(double kappa, double D1, double ds1, double f12, double D2, double ds2, double f21)
+{
+    const double C = 2.0 / 3.0;
+    double num = (((kappa * ds1) / D1) * f12) * C;
+    double den = 1.0 + ((kappa / 2.0) * (((ds1 / D1) * f12) + ((ds2 / D2) * f21))) * C;
+    return num / den;
+}
+
+/* (c_to / c_from)^lambda for the walker's side `from`: lambda fixed (the
+ * label of lower index is side 1, so the other side uses 1 - lambda) or,
+ * for lambda < 0, the minimiser of alpha_lambda,
+ * 1 / (1 + c_to sqrt(D_to) / (c_from sqrt(D_from))). */
+double rmso_conc_factor(double c_from, double c_to, double D_from, double D_to, double lambda, int from_is_side1)
+{
+    double lam;
+    if (lambda < 0.0)
+        lam = 1.0 / (1.0 + (c_to * sqrt(D_to)) / (c_from * sqrt(D_from)));
+    else
+        lam = from_is_side1 ? lambda : 1.0 - lambda;
+    return pow(c_to / c_from, lam);
+}
+
+/* App. C.3 (Baxter): P_{1->2} = c2 sqrt(D2) / (c1 sqrt(D1)) from the
+ * high-flux side, 1 from the other: min(1, that ratio) either way. */
+double rmso_perm_prob_baxter(double c1, double D1, double c2, double D2)
+{
+    return (c2 * sqrt(D2)) / (c1 * sqrt(D1));
 }
 
 /* Sec. 2.1.3 (magnetization transfer): the probability that a walker of
@@ -231,6 +278,10 @@ static int build_ctx(const rmso_config *cfg, ctx *X)
     int L = cfg->n_labels;
     memset(X, 0, sizeof(*X));
     X->cfg = cfg;
+    if (cfg->lambda > 1.0) return RMSO_ERR_BAD_ARG;
+    if (cfg->conc)
+        for (int c = 0; c < L; c++)
+            if (!cfg->dead[c] && !(cfg->conc[c] > 0.0)) return RMSO_ERR_BAD_ARG;
     X->s = (double *)malloc(sizeof(double) * L);
     for (int m = 0; m < 3; m++) X->dtR[m] = (double *)calloc(L, sizeof(double));
     X->T = (uint32_t *)calloc((size_t)L * L, sizeof(uint32_t));
@@ -253,8 +304,34 @@ static int build_ctx(const rmso_config *cfg, ctx *X)
                 X->T[(size_t)a * L + b] = 0u;
                 continue;
             }
-            X->T[(size_t)a * L + b] = rmso_threshold(rmso_perm_prob(k, cfg->D[a], ds[a], cfg->D[b], ds[b]));
+            double P;
+            const double ca = cfg->conc ? cfg->conc[a] : 1.0, cb = cfg->conc ? cfg->conc[b] : 1.0;
+            if (cfg->perm_model == RMSO_PERM_BAXTER) {
+                P = rmso_perm_prob_baxter(ca, cfg->D[a], cb, cfg->D[b]);
+            } else if (cfg->conc) {
+                double fab = rmso_conc_factor(ca, cb, cfg->D[a], cfg->D[b], cfg->lambda, a < b);
+                double fba = rmso_conc_factor(cb, ca, cfg->D[b], cfg->D[a], cfg->lambda, b < a);
+                P = rmso_perm_prob_conc(k, cfg->D[a], ds[a], fab, cfg->D[b], ds[b], fba);
+            } else {
+                P = rmso_perm_prob(k, cfg->D[a], ds[a], cfg->D[b], ds[b]);
+            }
+            X->T[(size_t)a * L + b] = rmso_threshold(P);
         }
+    if (cfg->conc) {
+        /* initial density proportional to the spin concentration (the
+         * equilibrium rho1/rho2 = c1/c2 of App. C.2): a uniform start in
+         * label l is kept with probability c_l / c_max */
+        double cmax = 0.0;
+        for (int c = 0; c < L; c++)
+            if (!cfg->dead[c] && cfg->conc[c] > cmax) cmax = cfg->conc[c];
+        X->acc = (uint64_t *)calloc(L, sizeof(uint64_t));
+        if (!X->acc) {
+            free(ds);
+            return RMSO_ERR_OOM;
+        }
+        for (int c = 0; c < L; c++)
+            X->acc[c] = cfg->dead[c] ? 0u : (uint64_t)floor((cfg->conc[c] / cmax) * 4294967296.0);
+    }
     if (cfg->rho) {
         X->Tmt = (uint32_t *)calloc((size_t)L * L, sizeof(uint32_t));
         if (!X->Tmt) {
@@ -293,6 +370,7 @@ static void free_ctx(ctx *X)
     for (int m = 0; m < 3; m++) free(X->dtR[m]);
     free(X->T);
     free(X->Tmt);
+    free(X->acc);
     free(X->ok_list);
 }
 
@@ -325,15 +403,24 @@ static int64_t flat_index(const rmso_config *cfg, const int64_t i[3])
 /* Sec. 2.2 item 1.  r = x0 << 32 | x1 from INIT call 0 picks the voxel
  * floor(r n_ok / 2^64) of the raster list; the offset inside it is
  * (u(x2), u(x3), u(y0)) with y from INIT call 1. */
-static void init_walker(const ctx *X, uint64_t w, walker *s)
+/* Sec. 2.2 item 1.  Attempt j uses INIT calls 2j and 2j + 1; with spin
+ * concentrations a start in label l is kept iff word 1 of call 2j + 1 is
+ * below acc[l] (at most RMSO_MAX_INIT attempts; returns 1 if none was
+ * kept, the last one then stands). */
+static int init_walker(const ctx *X, uint64_t w, walker *s)
 {
     const rmso_config *cfg = X->cfg;
     uint32_t x[4], y[4];
-    draw(cfg->seed, w, 0u, TAG_INIT, 0u, x);
-    draw(cfg->seed, w, 0u, TAG_INIT, 1u, y);
-    uint64_t r = ((uint64_t)x[0] << 32) | (uint64_t)x[1];
-    int64_t idx = (int64_t)(((unsigned __int128)r * (unsigned __int128)(uint64_t)X->n_ok) >> 64);
-    int64_t v = X->ok_list ? X->ok_list[idx] : idx;
+    int64_t v = 0;
+    int ok = 0;
+    for (uint32_t j = 0; j < RMSO_MAX_INIT && !ok; j++) {
+        draw(cfg->seed, w, 0u, TAG_INIT, 2u * j, x);
+        draw(cfg->seed, w, 0u, TAG_INIT, 2u * j + 1u, y);
+        uint64_t r = ((uint64_t)x[0] << 32) | (uint64_t)x[1];
+        int64_t idx = (int64_t)(((unsigned __int128)r * (unsigned __int128)(uint64_t)X->n_ok) >> 64);
+        v = X->ok_list ? X->ok_list[idx] : idx;
+        ok = !X->acc || (uint64_t)y[1] < X->acc[cfg->labels[v]];
+    }
     s->i[0] = v % cfg->nx;
     s->i[1] = (v / cfg->nx) % cfg->ny;
     s->i[2] = v / ((int64_t)cfg->nx * cfg->ny);
@@ -349,6 +436,7 @@ static void init_walker(const ctx *X, uint64_t w, walker *s)
     for (int k = 0; k < 3 * cfg->n_shapes; k++) s->phase[k] = 0.0;
     s->h = 0;
     s->n_events = s->n_cross = s->n_refl = 0;
+    return !ok;
 }
 
 /* Sec. 2.2 item 2, direction sampler (the paper does not name one):
@@ -662,7 +750,7 @@ static void *run_range(void *arg)
         return NULL;
     }
     for (int64_t w = J->wb; w < J->we; w++) {
-        init_walker(X, (uint64_t)w, &s);
+        if (init_walker(X, (uint64_t)w, &s)) J->err |= RMSO_ERR_INIT;
         int r = 0;
         for (int64_t k = 1; k <= cfg->n_steps; k++) {
             double n[3];

@@ -50,6 +50,11 @@ class Workload:
                random leap (the particle-membrane interaction of a run)
     rho        float64 (L, L) surface relaxivity (um/ms) of the membrane met from
                label r towards label c (magnetization transfer), or None
+    conc       float64 per label spin concentration, or None (all equal)
+    lam        exponent lambda of (c2/c1) in the generalised permeation
+               probability, in [0, 1]; < 0 picks the minimiser of alpha_lambda
+    perm_model 0 nominal permeability kappa, 1 Baxter's concentration rule
+               (kappa > 0 then only marks a permeable pair)
     """
     name: str
     labels: np.ndarray
@@ -71,6 +76,9 @@ class Workload:
     seed: int
     interaction: int = 0
     rho: Optional[np.ndarray] = None
+    conc: Optional[np.ndarray] = None
+    lam: float = -1.0
+    perm_model: int = 0
 
     @property
     def n_labels(self) -> int:

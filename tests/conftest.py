@@ -17,7 +17,8 @@ def pytest_configure(config):
 
 def make_workload(labels, voxel_um=0.2, D=2.0, kappa=0.0, T2=math.inf, T1=math.inf, dt=1e-3,
                   n_steps=100, G=None, dirs=None, b=None, rec_steps=None, n_walkers=1000, seed=1,
-                  periodic=(1, 1, 1), dead=None, mode=None, name="test", interaction=0, rho=None):
+                  periodic=(1, 1, 1), dead=None, mode=None, name="test", interaction=0, rho=None, conc=None,
+                  lam=-1.0, perm_model=0):
     """A Workload from per-label scalars or arrays (tests only)."""
     import rms_inputs as ri
     labels = np.ascontiguousarray(labels, dtype=np.uint16)
@@ -47,7 +48,8 @@ def make_workload(labels, voxel_um=0.2, D=2.0, kappa=0.0, T2=math.inf, T1=math.i
     return ri.Workload(name, labels, float(voxel_um), tuple(int(p) for p in periodic), Dv, T2v, T1v, K,
                        dead, float(dt), int(n_steps), G, mode, np.asarray(dirs, np.float64),
                        np.asarray(b, np.float64), np.asarray(rec_steps, np.int64), int(n_walkers), int(seed),
-                       int(interaction), _pair_table(rho, L))
+                       int(interaction), _pair_table(rho, L),
+                       None if conc is None else np.asarray(conc, np.float64), float(lam), int(perm_model))
 
 
 def _pair_table(v, L):
