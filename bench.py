@@ -239,7 +239,8 @@ def main():
     sp = stream.cuda_stream
 
     sub = rms.rms_create_substrate(wl.labels, wl.voxel_um, wl.D, T2=wl.T2, T1=wl.T1, kappa=wl.kappa,
-                                   dead=wl.dead, periodic=wl.periodic, stream=sp, rho=wl.rho)
+                                   dead=wl.dead, periodic=wl.periodic, stream=sp, rho=wl.rho, conc=wl.conc,
+                                   lam=wl.lam, perm_model=wl.perm_model)
     seq = rms.rms_set_sequence(sub, wl.dt, wl.G, wl.dirs, wl.b, wl.rec_steps, mode=wl.mode)
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
@@ -497,7 +498,8 @@ def e2e(rms, torch, wl, W, w_begin, sp, args, world, max_over_ranks):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sub = rms.rms_create_substrate(lab, wl.voxel_um, wl.D, T2=wl.T2, T1=wl.T1, kappa=wl.kappa, dead=wl.dead,
-                                       periodic=wl.periodic, stream=sp, rho=wl.rho)
+                                       periodic=wl.periodic, stream=sp, rho=wl.rho, conc=wl.conc, lam=wl.lam,
+                                       perm_model=wl.perm_model)
         seq = rms.rms_set_sequence(sub, wl.dt, wl.G, wl.dirs, wl.b, wl.rec_steps, mode=wl.mode)
         run = rms.rms_run(seq, W, wl.seed, rms.RMS_FP32, 0, w_begin, 0, sp, wl.interaction)
         rms.rms_read_signal(run)

@@ -81,6 +81,11 @@ typedef int rms_status;
 #define RMS_ERL 2
 #define RMS_MAX_LEAPS 64
 
+/* Permeation models of rms_substrate_desc.perm_model (Sec. 2.1.3, App. C) */
+#define RMS_PERM_KAPPA 0
+#define RMS_PERM_BAXTER 1
+#define RMS_MAX_INIT 4096 /* start draws per walker with spin concentrations */
+
 typedef struct rms_substrate rms_substrate;
 typedef struct rms_sequence rms_sequence;
 typedef struct rms_run_handle rms_run_handle;
@@ -115,6 +120,22 @@ typedef struct {
                                  with probability P_MT = (rho ds_r / D_r) C_3 (C_3 = 2/3; clamped to
                                  1 with RMS_W_PROB_RANGE), after which its weight is 0.  A membrane
                                  into a dead label counts; diagonal ignored; NULL: none */
+    const double *conc;       /* host, L or NULL (all equal): spin concentration per label, > 0 for
+                                 every live label (App. C.2).  Walkers start with density ~ c (a
+                                 uniform start in label l is kept with probability c_l / c_max, at
+                                 most RMS_MAX_INIT draws; RMS_E_INVALID_ARG when the volume mean of
+                                 c / c_max is below 1/200), and permeation keeps the equilibrium
+                                 density ratio c1/c2 */
+    double lambda;            /* RMS_PERM_KAPPA with conc: P_{1->2} carries (c2/c1)^lambda and
+                                 P_{2->1} (c2/c1)^(lambda-1), with the finite-step correction
+                                 kappa = kappa0 / (1 - alpha_lambda); lambda in [0,1] with the label
+                                 of lower index as side 1, or < 0 for the alpha-minimising lambda =
+                                 1 / (1 + c2 sqrt(D2) / (c1 sqrt(D1))) */
+    int32_t perm_model;       /* RMS_PERM_KAPPA (0): nominal permeability kappa, Eq. 3 (generalised
+                                 when conc is given); RMS_PERM_BAXTER: P_{1->2} = c2 sqrt(D2) /
+                                 (c1 sqrt(D1)) from the high-flux side, 1 from the other (App. C.3;
+                                 its effective permeability grows as 1/sqrt(dt)); kappa > 0 then
+                                 only marks which pairs are permeable */
     const uint8_t *dead;      /* host, L or NULL: 1 = no walker starts in or enters the label */
     void *stream;             /* cudaStream_t for the upload */
 } rms_substrate_desc;

@@ -160,7 +160,7 @@ typedef struct {
 #define RMSO_ERR_LEAPS 16 /* an ERL step found no admissible direction in RMSO_MAX_LEAPS draws */
 #define RMSO_PERM_KAPPA 0
 #define RMSO_PERM_BAXTER 1
-#define RMSO_MAX_INIT 256
+#define RMSO_MAX_INIT 4096
 #define RMSO_ERR_INIT 32  /* a walker found no accepted start in RMSO_MAX_INIT draws */
 
 typedef struct {

@@ -29,6 +29,8 @@ RMS_EC = 0
 RMS_RS = 1
 RMS_ERL = 2
 RMS_MAX_LEAPS = 64
+RMS_PERM_KAPPA = 0
+RMS_PERM_BAXTER = 1
 
 
 class RmsError(RuntimeError):
@@ -42,7 +44,8 @@ class SubstrateDesc(C.Structure):
                 ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("voxel_um", C.c_double), ("periodic", C.c_int32 * 3), ("n_labels", C.c_int32),
                 ("D", C.c_void_p), ("T2", C.c_void_p), ("T1", C.c_void_p), ("kappa", C.c_void_p),
-                ("kappa_scalar", C.c_double), ("rho", C.c_void_p), ("dead", C.c_void_p), ("stream", C.c_void_p)]
+                ("kappa_scalar", C.c_double), ("rho", C.c_void_p), ("conc", C.c_void_p), ("lam", C.c_double),
+                ("perm_model", C.c_int32), ("dead", C.c_void_p), ("stream", C.c_void_p)]
 
 
 class SequenceDesc(C.Structure):

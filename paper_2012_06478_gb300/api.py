@@ -110,9 +110,13 @@ class Run:
 
 def rms_create_substrate(labels, voxel_um: float, D, T2=None, T1=None, kappa=None, kappa_scalar: float = 0.0,
                          dead=None, periodic=(1, 1, 1), n_labels: Optional[int] = None,
-                         stream: Optional[int] = None, rho=None) -> Substrate:
+                         stream: Optional[int] = None, rho=None, conc=None, lam: float = -1.0,
+                         perm_model: int = 0) -> Substrate:
     """labels: (nz, ny, nx) uint16 numpy array or CUDA tensor (x fastest).
-    rho: optional (L, L) surface relaxivity (um/ms) of absorbing membranes."""
+    rho: optional (L, L) surface relaxivity (um/ms) of absorbing membranes.
+    conc, lam, perm_model: spin concentration per label, the exponent lambda
+    (< 0: the optimal one) and the permeation model (0 nominal kappa,
+    1 Baxter)."""
     on_device = hasattr(labels, "is_cuda") and labels.is_cuda
     if on_device:
         import torch
@@ -130,6 +134,7 @@ def rms_create_substrate(labels, voxel_um: float, D, T2=None, T1=None, kappa=Non
     T2v, T1v = _host(T2, np.float64), _host(T1, np.float64)
     Kv = _host(kappa, np.float64)
     Rv = _host(rho, np.float64)
+    Cv = _host(conc, np.float64)
     deadv = _host(dead, np.uint8)
     d = L.SubstrateDesc()
     d.labels = lab_ptr
@@ -141,6 +146,9 @@ def rms_create_substrate(labels, voxel_um: float, D, T2=None, T1=None, kappa=Non
     d.D, d.T2, d.T1, d.kappa = _ptr(Dv), _ptr(T2v), _ptr(T1v), _ptr(Kv)
     d.kappa_scalar = float(kappa_scalar)
     d.rho = _ptr(Rv)
+    d.conc = _ptr(Cv)
+    d.lam = float(lam)
+    d.perm_model = int(perm_model)
     d.dead = _ptr(deadv)
     d.stream = current_stream() if stream is None else stream
     h = C.c_void_p()
@@ -253,7 +261,9 @@ def simulate(wl, precision: int = RMS_FP64, n_walkers: Optional[int] = None, see
     The interaction defaults to the workload's (elastic collision if unset);
     `leap_limit` in the result is True when an ERL step used up its draws."""
     sub = rms_create_substrate(wl.labels, wl.voxel_um, wl.D, T2=wl.T2, T1=wl.T1, kappa=wl.kappa, dead=wl.dead,
-                               periodic=wl.periodic, stream=stream, rho=getattr(wl, "rho", None))
+                               periodic=wl.periodic, stream=stream, rho=getattr(wl, "rho", None),
+                               conc=getattr(wl, "conc", None), lam=getattr(wl, "lam", -1.0),
+                               perm_model=getattr(wl, "perm_model", 0))
     G = np.asarray(wl.G, np.float64)
     G = G.reshape(-1, wl.n_steps) if wl.n_steps else np.zeros((G.shape[0] if G.ndim == 2 else 1, 0))
     seq = rms_set_sequence(sub, wl.dt, G, wl.dirs, wl.b, wl.rec_steps, mode=wl.mode)

@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "librms.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
           "--expt-relaxed-constexpr"]
-UNITS = [("rms_api.cu", ["-fmad=false"]), ("walk_fp64.cu", ["-fmad=false"]), ("walk_fp32.cu", ["-fmad=true"]),
+UNITS = [("rms_api.cu", ["-fmad=false", "-Xcompiler", "-ffp-contract=off"]), ("walk_fp64.cu", ["-fmad=false"]), ("walk_fp32.cu", ["-fmad=true"]),
          ("walk_reject_fp64.cu", ["-fmad=false"]), ("walk_reject_fp32.cu", ["-fmad=true"]),
          ("walk_mt_fp64.cu", ["-fmad=false"]), ("walk_mt_fp32.cu", ["-fmad=true"]),
          ("rms_noalloc.cu", ["-fmad=false"]), ("rms_serve.cu", ["-fmad=false"])]

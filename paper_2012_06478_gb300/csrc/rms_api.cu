@@ -267,17 +267,26 @@ __global__ void bvalue_kernel(int64_t N, int32_t S, double dt, const double *G, 
 // ------------------------------------------------------------------ init (Sec. 2.2 item 1)
 
 template <typename Real>
-__global__ void init_kernel(Geometry g, const int32_t *ok_list, int64_t n_ok, WalkerState<Real> st,
-                            RunCtl ctl, bool hash)
+__global__ void init_kernel(Geometry g, const int32_t *ok_list, int64_t n_ok, const uint64_t *acc,
+                            WalkerState<Real> st, RunCtl ctl, bool hash)
 {
     const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (li >= ctl.n_walkers) return;
     const uint64_t w = (uint64_t)(ctl.w_begin + li);
-    const U4 x = draw(ctl.seed, w, 0u, kTagInit, 0u);
-    const U4 y = draw(ctl.seed, w, 0u, kTagInit, 1u);
-    const uint64_t r = ((uint64_t)x.x << 32) | (uint64_t)x.y;
-    const int64_t idx = (int64_t)__umul64hi(r, (uint64_t)n_ok);
-    const int64_t vox = ok_list ? (int64_t)ok_list[idx] : idx;
+    // attempt j: INIT calls 2j, 2j + 1; with spin concentrations the start in
+    // label l is kept iff word 1 of call 2j + 1 is below acc[l] (density ~ c)
+    U4 x, y;
+    int64_t vox = 0;
+    bool ok = false;
+    for (uint32_t j = 0; j < kMaxInit && !ok; ++j) {
+        x = draw(ctl.seed, w, 0u, kTagInit, 2u * j);
+        y = draw(ctl.seed, w, 0u, kTagInit, 2u * j + 1u);
+        const uint64_t r = ((uint64_t)x.x << 32) | (uint64_t)x.y;
+        const int64_t idx = (int64_t)__umul64hi(r, (uint64_t)n_ok);
+        vox = ok_list ? (int64_t)ok_list[idx] : idx;
+        ok = acc == nullptr || (uint64_t)y.y < acc[g.labels[vox]];
+    }
+    if (!ok) atomicOr(ctl.status, kErrInit);
     const int32_t ix = (int32_t)(vox % g.nx);
     const int32_t iy = (int32_t)((vox / g.nx) % g.ny);
     const int32_t iz = (int32_t)(vox / ((int64_t)g.nx * g.ny));
@@ -448,8 +457,48 @@ static void free_substrate(rms_substrate *s, cudaStream_t st)
     cudaFreeAsync(s->d_T1, st);
     cudaFreeAsync(s->d_kappa, st);
     if (s->d_rho) cudaFreeAsync(s->d_rho, st);
+    if (s->d_acc) cudaFreeAsync(s->d_acc, st);
     cudaFreeAsync(s->d_dead, st);
     if (s->d_ok) cudaFreeAsync(s->d_ok, st);
+}
+
+__global__ void label_hist_kernel(const uint16_t *labels, int64_t n, unsigned long long *count)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(count + labels[i], 1ull);
+}
+
+// App. C.2: walkers start with density proportional to the spin
+// concentration -- a uniform start in label l is kept iff a 32-bit word is
+// below acc[l] = floor(c_l / c_max 2^32).  Rejects contrasts whose
+// acceptance rate (the volume mean of c / c_max) is below 1/200, for which
+// kMaxInit draws could run out.
+static rms_status concentration_tables(rms_substrate *s, int64_t nvox, cudaStream_t st)
+{
+    const int L = s->L;
+    unsigned long long *d_cnt = nullptr;
+    RMS_CUDA(cudaMallocAsync((void **)&d_cnt, sizeof(unsigned long long) * L, st));
+    RMS_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * L, st));
+    label_hist_kernel<<<1024, 256, 0, st>>>(s->d_labels, nvox, d_cnt);
+    RMS_CUDA(cudaGetLastError());
+    std::vector<unsigned long long> cnt(L);
+    RMS_CUDA(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(unsigned long long) * L, cudaMemcpyDeviceToHost, st));
+    RMS_CUDA(cudaFreeAsync(d_cnt, st));
+    RMS_CUDA(cudaStreamSynchronize(st));
+    double cmax = 0.0, sum_cv = 0.0, sum_v = 0.0;
+    for (int l = 0; l < L; ++l)
+        if (!s->dead[l] && s->conc[l] > cmax) cmax = s->conc[l];
+    std::vector<uint64_t> acc(L, 0);
+    for (int l = 0; l < L; ++l) {
+        if (s->dead[l]) continue;
+        acc[l] = (uint64_t)std::floor((s->conc[l] / cmax) * 4294967296.0);
+        sum_cv += s->conc[l] * (double)cnt[l];
+        sum_v += (double)cnt[l];
+    }
+    if (sum_v > 0.0 && sum_cv / (cmax * sum_v) < 1.0 / 200.0)
+        return fail(RMS_E_INVALID_ARG, "spin concentration contrast too large: volume mean of c / c_max < 1/200");
+    RMS_TRY(upload(&s->d_acc, acc.data(), (size_t)L, st));
+    return RMS_OK;
 }
 
 static rms_status create_substrate_impl(const rms_substrate_desc *d, rms_substrate *s)
@@ -473,6 +522,12 @@ static rms_status create_substrate_impl(const rms_substrate_desc *d, rms_substra
     else
         s->kappa.assign((size_t)L * L, d->kappa_scalar);
     if (d->rho) s->rho.assign(d->rho, d->rho + (size_t)L * L);
+    if (d->conc) s->conc.assign(d->conc, d->conc + L);
+    s->lambda = d->lambda;
+    s->perm_model = d->perm_model;
+    if (s->perm_model != RMS_PERM_KAPPA && s->perm_model != RMS_PERM_BAXTER)
+        return fail(RMS_E_INVALID_ARG, "perm_model must be RMS_PERM_KAPPA or RMS_PERM_BAXTER");
+    if (!(s->lambda <= 1.0)) return fail(RMS_E_INVALID_ARG, "lambda must be <= 1 (< 0: the optimal lambda)");
     s->dead.assign(L, 0);
     if (d->dead)
         for (int c = 0; c < L; ++c) s->dead[c] = d->dead[c] ? 1 : 0;
@@ -488,6 +543,9 @@ static rms_status create_substrate_impl(const rms_substrate_desc *d, rms_substra
     for (size_t k = 0; k < s->rho.size(); ++k)
         if (!(s->rho[k] >= 0.0) || !std::isfinite(s->rho[k]))
             return fail(RMS_E_INVALID_ARG, "rho must be finite and >= 0");
+    for (size_t k = 0; k < s->conc.size(); ++k)
+        if (!s->dead[k] && (!(s->conc[k] > 0.0) || !std::isfinite(s->conc[k])))
+            return fail(RMS_E_INVALID_ARG, "conc must be finite and > 0 for every live label (mark c = 0 dead)");
     RMS_TRY(upload(&s->d_labels, d->labels, (size_t)nvox, st, d->labels_on_device != 0));
     RMS_TRY(upload(&s->d_D, s->D.data(), L, st));
     RMS_TRY(upload(&s->d_T2, s->T2.data(), L, st));
@@ -506,6 +564,7 @@ static rms_status create_substrate_impl(const rms_substrate_desc *d, rms_substra
     RMS_CUDA(cudaFreeAsync(d_max, st));
     RMS_CUDA(cudaStreamSynchronize(st));
     if ((int64_t)mx >= L) return fail(RMS_E_INVALID_ARG, "a label value is >= n_labels");
+    if (!s->conc.empty()) RMS_TRY(concentration_tables(s, nvox, st));
     bool any_dead = false;
     for (int c = 0; c < L; ++c) any_dead |= s->dead[c] != 0;
     if (!any_dead) {
@@ -571,6 +630,60 @@ extern "C" rms_status rms_destroy_substrate(rms_substrate *s)
 }
 
 // ------------------------------------------------------------------ sequence
+
+// Bernoulli threshold: min(floor(P 2^32), 2^32 - 1); 0 for P <= 0.
+static uint32_t threshold_of(double P)
+{
+    if (!(P > 0.0)) return 0u;
+    if (P >= 1.0) return 0xFFFFFFFFu;
+    const double x = std::floor(P * 4294967296.0);
+    return x >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)x;
+}
+
+// (c_to / c_from)^lambda seen from the walker's side: lambda fixed (the
+// label of lower index is side 1, the other side uses 1 - lambda) or, for
+// lambda < 0, the minimiser of alpha_lambda (App. C.2).
+static double conc_factor(double c_from, double c_to, double D_from, double D_to, double lambda, bool side1)
+{
+    const double lam = lambda < 0.0 ? 1.0 / (1.0 + (c_to * std::sqrt(D_to)) / (c_from * std::sqrt(D_from)))
+                                    : (side1 ? lambda : 1.0 - lambda);
+    return std::pow(c_to / c_from, lam);
+}
+
+// Permeation thresholds with spin concentrations (App. C.2, the generalised
+// Eq. 3 with the finite-step correction kappa = kappa0 / (1 - alpha_lambda))
+// or by Baxter's rule (App. C.3, P = c2 sqrt(D2) / (c1 sqrt(D1)), at most 1;
+// kappa > 0 marks the permeable pairs).  Computed on the host because the
+// generalised form needs pow: this unit is built with -ffp-contract=off and
+// the operations follow the order written, so the thresholds are the same
+// bits as any IEEE evaluation of that order with the same libm.
+static void host_pair_tables(const rms_substrate *sub, double dt, std::vector<uint32_t> &T, bool &warn)
+{
+    const int L = sub->L;
+    const double C = 2.0 / 3.0;
+    std::vector<double> ds(L);
+    for (int c = 0; c < L; ++c) ds[c] = std::sqrt((6.0 * sub->D[c]) * dt);
+    T.assign((size_t)L * L, 0u);
+    for (int a = 0; a < L; ++a)
+        for (int b = 0; b < L; ++b) {
+            const double k = sub->kappa[(size_t)a * L + b];
+            if (a == b || sub->dead[a] || sub->dead[b] || !(k > 0.0)) continue;
+            const double ca = sub->conc.empty() ? 1.0 : sub->conc[a];
+            const double cb = sub->conc.empty() ? 1.0 : sub->conc[b];
+            double P;
+            if (sub->perm_model == RMS_PERM_BAXTER) {
+                P = (cb * std::sqrt(sub->D[b])) / (ca * std::sqrt(sub->D[a]));
+            } else {
+                const double fab = conc_factor(ca, cb, sub->D[a], sub->D[b], sub->lambda, a < b);
+                const double fba = conc_factor(cb, ca, sub->D[b], sub->D[a], sub->lambda, b < a);
+                const double num = (((k * ds[a]) / sub->D[a]) * fab) * C;
+                const double den = 1.0 + ((k / 2.0) * (((ds[a] / sub->D[a]) * fab) + ((ds[b] / sub->D[b]) * fba))) * C;
+                P = num / den;
+                if (P > 1.0) warn = true;
+            }
+            T[(size_t)a * L + b] = threshold_of(P);
+        }
+}
 
 static void free_sequence(rms_sequence *q, cudaStream_t st)
 {
@@ -645,6 +758,12 @@ static rms_status set_sequence_impl(rms_substrate *sub, const rms_sequence_desc 
     if (sub->d_rho)
         mt_tables_kernel<<<(unsigned)((LL + 255) / 256), 256, 0, st>>>(L, sub->d_D, sub->d_rho, sub->d_dead,
                                                                         d->dt_ms, q->d_Tmt, d_warn);
+    std::vector<uint32_t> hostT;  // lives until the stream synchronisation below
+    bool host_warn = false;
+    if (!sub->conc.empty() || sub->perm_model == RMS_PERM_BAXTER) {
+        host_pair_tables(sub, d->dt_ms, hostT, host_warn);
+        RMS_CUDA(cudaMemcpyAsync(q->d_T, hostT.data(), sizeof(uint32_t) * hostT.size(), cudaMemcpyHostToDevice, st));
+    }
     if (N > 0)
         step_tables_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, S, d->dt_ms, d_G, d_rec, d->n_rec,
                                                                          q->d_wG64, q->d_wG32, q->d_flags,
@@ -657,7 +776,7 @@ static rms_status set_sequence_impl(rms_substrate *sub, const rms_sequence_desc 
     RMS_CUDA(cudaFreeAsync(d_rec, st));
     RMS_CUDA(cudaFreeAsync(d_warn, st));
     RMS_CUDA(cudaStreamSynchronize(st));
-    *warn = w != 0;
+    *warn = w != 0 || host_warn;
     return RMS_OK;
 }
 
@@ -772,8 +891,8 @@ static rms_status init_impl(rms_run_handle *r)
 {
     const ReqDesc<Real> d = run_desc<Real>(r);
     const unsigned ib = (unsigned)((r->W + 255) / 256);
-    init_kernel<Real><<<ib, 256, 0, r->stream>>>(d.g, r->seq->sub->d_ok, r->seq->sub->n_ok, d.st, d.ctl,
-                                                  (r->flags & RMS_TRAJ_HASH) != 0);
+    init_kernel<Real><<<ib, 256, 0, r->stream>>>(d.g, r->seq->sub->d_ok, r->seq->sub->n_ok, r->seq->sub->d_acc, d.st,
+                                                  d.ctl, (r->flags & RMS_TRAJ_HASH) != 0);
     RMS_CUDA(cudaGetLastError());
     return RMS_OK;
 }

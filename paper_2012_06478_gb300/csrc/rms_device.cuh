@@ -84,7 +84,8 @@ constexpr int kMaxShapes = 8;
 
 // Device status bits: errors, and one warning (an ERL step that found no
 // admissible direction in kMaxLeaps draws; the walker stayed for that step).
-enum : int { kErrTimeout = 4, kWarnLeaps = 8 };
+enum : int { kErrTimeout = 4, kWarnLeaps = 8, kErrInit = 16 };
+constexpr uint32_t kMaxInit = 4096;  // start draws per walker (spin concentrations)
 
 // A saturated walker (Sec. 2.1.3, magnetization transfer) has weight 0 for
 // good.  The FP64 form keeps A = +inf, as the CPU reference does; the FP32

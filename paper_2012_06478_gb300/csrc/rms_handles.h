@@ -19,6 +19,10 @@ struct rms_substrate {
     int32_t L = 0;
     std::vector<double> D, T2, T1, kappa;
     std::vector<double> rho;  // surface relaxivity per pair (empty: no absorbing membrane)
+    std::vector<double> conc; // spin concentration per label (empty: all equal)
+    double lambda = -1.0;     // exponent of (c2/c1) in the generalised Eq. 3 (< 0: optimal)
+    int32_t perm_model = RMS_PERM_KAPPA;
+    uint64_t *d_acc = nullptr;  // per label start acceptance threshold (nullptr: always)
     std::vector<uint8_t> dead;
     uint16_t *d_labels = nullptr;
     double *d_D = nullptr, *d_T2 = nullptr, *d_T1 = nullptr, *d_kappa = nullptr, *d_rho = nullptr;
