@@ -125,12 +125,12 @@ def events_per_step(wl):
     return float((frac * 1.5 * ds / wl.voxel_um).sum())
 
 
-def cpu_baseline(wl, seconds=12.0):
+def cpu_baseline(wl, seconds=12.0, threads=0):
     """The oracle as it stands on this host's cores, on a walker sample of the
     same workload (walkers are independent: the sample's rate is the run's)."""
     import oracle
     oracle.build()
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     probe = max(cores, 16)
     t0 = time.perf_counter()
     oracle.run(wl, 0, probe, n_threads=cores, hash_=False)
@@ -153,7 +153,7 @@ def run_reference(args):
     wl = workload_of(args.workload, args.interaction, args.rho)
     import oracle
     oracle.build()
-    cores = os.cpu_count() or 1
+    cores = args.cpu_threads or os.cpu_count() or 1
     probe = max(cores, 16)
     t0 = time.perf_counter()
     oracle.run(wl, 0, probe, n_threads=cores, hash_=False)
@@ -208,6 +208,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64 plain-form steps")
     ap.add_argument("--fp64-warmup", type=int, default=1, help="untimed FP64 plain-form steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-threads", type=int, default=0,
+                    help="host threads for the oracle legs (cpu_baseline, --impl reference); 0: all cores")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=512)
     ap.add_argument("--serving-fp64", action="store_true", help="also serve the stream in the FP64 plain form")
@@ -369,7 +371,7 @@ def main():
         if args.serving_fp64 and value64:
             line["serving_fp64"] = serving(rms, ri, value64, args.serving_requests, rms.RMS_FP64, sp)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl)
+        line["cpu_baseline"] = cpu_baseline(wl, threads=args.cpu_threads)
     seq.close()
     sub.close()
     if rank == 0:
