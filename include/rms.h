@@ -59,6 +59,11 @@ typedef int rms_status;
 
 /* rms_run flags */
 #define RMS_TRAJ_HASH 1u /* keep a per-walker 64-bit checksum of the (step, voxel, label) sequence */
+#define RMS_CHECKED 2u   /* verify the walker invariants after every step -- voxel coordinates in range,
+                            flat index consistent with them, the walker's label equal to its voxel's,
+                            offsets in [0,1] -- in the verification kernel (the one that also keeps
+                            the checksum); a violation makes the read calls return RMS_E_DEVICE.
+                            Slower; for testing and debugging. */
 
 /* Particle-membrane interaction of rms_run (Sec. 2.1.2).  A face is "refused"
  * when it is impermeable (a label pair with kappa = 0, a dead label, the wall

@@ -25,6 +25,7 @@ RMS_E_NOT_READY = -10
 RMS_FP64 = 0
 RMS_FP32 = 1
 RMS_TRAJ_HASH = 1
+RMS_CHECKED = 2
 RMS_EC = 0
 RMS_RS = 1
 RMS_ERL = 2

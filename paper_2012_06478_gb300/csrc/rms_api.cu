@@ -878,6 +878,7 @@ ReqDesc<Real> rms::run_desc(rms_run_handle *r)
     d.ctl.n_shapes = q->S;
     d.ctl.n_rec = q->n_rec;
     d.ctl.status = r->d_status;
+    d.ctl.checked = (r->flags & RMS_CHECKED) != 0;
     d.ctl.cancel = r->d_cancel;
     d.ctl.mom_partial = r->d_mom_partial;
     d.ctl.n_blocks = r->n_blocks;
@@ -892,7 +893,7 @@ static rms_status init_impl(rms_run_handle *r)
     const ReqDesc<Real> d = run_desc<Real>(r);
     const unsigned ib = (unsigned)((r->W + 255) / 256);
     init_kernel<Real><<<ib, 256, 0, r->stream>>>(d.g, r->seq->sub->d_ok, r->seq->sub->n_ok, r->seq->sub->d_acc, d.st,
-                                                  d.ctl, (r->flags & RMS_TRAJ_HASH) != 0);
+                                                  d.ctl, (r->flags & (RMS_TRAJ_HASH | RMS_CHECKED)) != 0);
     RMS_CUDA(cudaGetLastError());
     return RMS_OK;
 }
@@ -906,7 +907,7 @@ template <typename Real>
 static rms_status walk_impl(rms_run_handle *r, int64_t k0, int64_t k1)
 {
     const ReqDesc<Real> d = run_desc<Real>(r);
-    const bool hash = (r->flags & RMS_TRAJ_HASH) != 0;
+    const bool hash = (r->flags & (RMS_TRAJ_HASH | RMS_CHECKED)) != 0;  // the verification kernel
     const dim3 grid((unsigned)r->n_blocks);
     const int S = r->seq->S;
 #define RMS_WALK(IM, MT) \
@@ -974,7 +975,7 @@ size_t rms::run_state_bytes(const rms_sequence *q, int64_t W, int32_t precision,
 {
     WalkerState<double> s64{};
     WalkerState<float> s32{};
-    const bool hash = (flags & RMS_TRAJ_HASH) != 0;
+    const bool hash = (flags & (RMS_TRAJ_HASH | RMS_CHECKED)) != 0;
     const int64_t nb = (W + kWalkBlockSize - 1) / kWalkBlockSize;
     const int64_t nc = (W + kRoChunk - 1) / kRoChunk;
     const int64_t ncombo = (int64_t)q->S * q->n_dirs * q->n_b;
@@ -990,7 +991,7 @@ rms_status rms::run_setup(rms_run_handle *r, bool with_cancel_and_events)
 {
     rms_sequence *q = r->seq;
     cudaStream_t s = r->stream;
-    const bool hash = (r->flags & RMS_TRAJ_HASH) != 0;
+    const bool hash = (r->flags & (RMS_TRAJ_HASH | RMS_CHECKED)) != 0;
     const bool f32 = r->precision == RMS_FP32;
     r->n_blocks = (int32_t)((r->W + walk_block_size() - 1) / walk_block_size());
     r->n_combo = q->S * q->n_dirs * q->n_b;
@@ -1038,7 +1039,7 @@ extern "C" rms_status rms_run(rms_sequence *q, const rms_run_desc *d, rms_run_ha
         return fail(RMS_E_INVALID_ARG, "n_walkers must be in [1, 2^31) and walker_begin >= 0");
     if (d->precision != RMS_FP64 && d->precision != RMS_FP32)
         return fail(RMS_E_INVALID_ARG, "precision must be RMS_FP64 or RMS_FP32");
-    if (d->flags & ~RMS_TRAJ_HASH) return fail(RMS_E_INVALID_ARG, "unknown flag");
+    if (d->flags & ~(RMS_TRAJ_HASH | RMS_CHECKED)) return fail(RMS_E_INVALID_ARG, "unknown flag");
     if (d->steps_per_launch < 0) return fail(RMS_E_INVALID_ARG, "steps_per_launch must be >= 0");
     if (d->interaction != RMS_EC && d->interaction != RMS_RS && d->interaction != RMS_ERL)
         return fail(RMS_E_INVALID_ARG, "interaction must be RMS_EC, RMS_RS or RMS_ERL");
@@ -1090,6 +1091,8 @@ static rms_status finish(rms_run_handle *r)
     if (*(volatile int32_t *)r->h_cancel) return fail(RMS_E_CANCELLED, "run was cancelled");
     int32_t status = 0;
     RMS_CUDA(cudaMemcpy(&status, r->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (status & kErrInvariant)
+        return fail(RMS_E_DEVICE, "a walker invariant broke (RMS_CHECKED); device status " + std::to_string(status));
     if (status & ~kWarnLeaps) return fail(RMS_E_DEVICE, "device status " + std::to_string(status));
     if (status & kWarnLeaps) {
         set_last_error("an ERL step found no admissible direction in RMS_MAX_LEAPS draws; "
@@ -1143,7 +1146,7 @@ extern "C" rms_status rms_read_walkers(rms_run_handle *r, int32_t *i, double *o,
     double *dp = (double *)(buf + offs[6]);
     uint64_t *dh = (uint64_t *)(buf + offs[7]);
     const unsigned nb = (unsigned)((W + 255) / 256);
-    const bool hsh = (r->flags & RMS_TRAJ_HASH) != 0;
+    const bool hsh = (r->flags & (RMS_TRAJ_HASH | RMS_CHECKED)) != 0;
     if (r->precision == RMS_FP32)
         export_kernel<float><<<nb, 256, 0, s>>>(r->st32, W, S, hsh, di, dO, di0, dO0, dc, dA, dp, dh);
     else

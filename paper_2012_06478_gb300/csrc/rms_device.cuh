@@ -84,7 +84,7 @@ constexpr int kMaxShapes = 8;
 
 // Device status bits: errors, and one warning (an ERL step that found no
 // admissible direction in kMaxLeaps draws; the walker stayed for that step).
-enum : int { kErrTimeout = 4, kWarnLeaps = 8, kErrInit = 16 };
+enum : int { kErrTimeout = 4, kWarnLeaps = 8, kErrInit = 16, kErrInvariant = 32 };
 constexpr uint32_t kMaxInit = 4096;  // start draws per walker (spin concentrations)
 
 // A saturated walker (Sec. 2.1.3, magnetization transfer) has weight 0 for
@@ -142,6 +142,7 @@ struct RunCtl {
     int32_t n_shapes;
     int32_t n_rec;
     int32_t *status;                // device error bits
+    int32_t checked;                // verify the walker invariants every step (verification kernel)
     const volatile int32_t *cancel; // host-mapped cancel flag (nullptr = none)
     double *mom_partial;            // [rec][block][22]
     int32_t n_blocks;

@@ -533,10 +533,20 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                 }
             }
             }  // draws
-            if (HASH) {
+            if (HASH) {  // the verification kernel: checksum and, on request, invariants
                 const uint64_t x = (((uint64_t)k & 0xFFFFu) << 48) ^ ((uint64_t)(uint32_t)c << 32) ^
                                    (uint64_t)(uint32_t)v;
                 h = mix64(h ^ x);
+                if (ctl.checked) {
+                    bool bad = false;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) bad = bad || wc[a] < 0 || wc[a] >= N[a];
+                    bad = bad || v != wc[0] + stride[1] * wc[1] + stride[2] * wc[2];
+                    if (!bad) bad = (int32_t)__ldg(g.labels + v) != c;  // indices checked first
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) bad = bad || !(o[a] >= Real(0) && o[a] <= Real(1));
+                    if (bad) atomicOr(ctl.status, kErrInvariant);
+                }
             }
             // ---- phase (Eq. 7, right end point of each step)
             if (fl & 1u) {
