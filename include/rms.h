@@ -212,6 +212,39 @@ typedef struct {
  * interaction), RMS_E_OOM, RMS_E_CUDA. */
 rms_status rms_run(rms_sequence *seq, const rms_run_desc *desc, rms_run_handle **out);
 
+/* A run's state after `step` steps, for resuming it (checkpoint/restart).
+ * Host arrays in the layouts rms_read_walkers writes; the caller keeps
+ * ownership (they are read before rms_run_range returns). */
+typedef struct {
+    int64_t step;            /* steps already taken, 0 <= step <= n_steps */
+    const int32_t *i;        /* W*3 unwrapped voxel index */
+    const double *o;         /* W*3 offset in [0,1] */
+    const int32_t *i0;       /* W*3 start voxel (wrapped) */
+    const double *o0;        /* W*3 start offset */
+    const int32_t *c;        /* W label */
+    const double *A;         /* W relaxation exponent of Eq. 5 (+INFINITY: saturated) */
+    const double *phase;     /* W*n_shapes*3 (may be NULL when n_shapes = 0) */
+    const uint64_t *hash;    /* W checksums, or NULL (0) */
+    const double *moments;   /* n_rec*22 moment sums (rms_read_signal layout) of the recording steps
+                                <= step, or NULL (zeros) */
+} rms_run_state;
+
+/* rms_run over part of the sequence: start from the initialisation (from ==
+ * NULL) or from a stored state (from->step steps taken, same W, walker_begin,
+ * seed, precision and interaction as the run that wrote it), and stop after
+ * step_end (0: n_steps).  The signal read afterwards is that of the phases
+ * at step_end; moment sums of recording steps beyond step_end are 0.  The
+ * random streams depend only on (seed, walker, step), so in the plain FP64
+ * form a run split at any step and resumed gives the uninterrupted run's
+ * walkers, checksums, moments and signal bit for bit; the FP32 form resumes
+ * from the widened state (its Kahan terms restart from the float rounding of
+ * each value) and agrees to rounding.  rms_run(seq, desc, out) is
+ * rms_run_range(seq, desc, NULL, 0, out).  Errors as rms_run, and
+ * RMS_E_INVALID_ARG for a step range outside 0 <= from->step <= step_end <=
+ * n_steps or a missing array. */
+rms_status rms_run_range(rms_sequence *seq, const rms_run_desc *desc, const rms_run_state *from, int64_t step_end,
+                         rms_run_handle **out);
+
 /* RMS_OK when the run has finished, RMS_E_NOT_READY while in flight. */
 rms_status rms_run_query(rms_run_handle *run);
 

@@ -65,6 +65,12 @@ class RunDesc(C.Structure):
                 ("interaction", C.c_int32), ("stream", C.c_void_p)]
 
 
+class RunState(C.Structure):
+    _fields_ = [("step", C.c_int64), ("i", C.c_void_p), ("o", C.c_void_p), ("i0", C.c_void_p), ("o0", C.c_void_p),
+                ("c", C.c_void_p), ("A", C.c_void_p), ("phase", C.c_void_p), ("hash", C.c_void_p),
+                ("moments", C.c_void_p)]
+
+
 # name -> (argtypes, restype); the exported C entry points of include/rms.h
 SIGNATURES = {
     "rms_version": ([], C.c_int),
@@ -75,6 +81,8 @@ SIGNATURES = {
     "rms_sequence_bvalues": ([C.c_void_p, C.c_void_p], C.c_int),
     "rms_destroy_sequence": ([C.c_void_p], C.c_int),
     "rms_run": ([C.c_void_p, C.POINTER(RunDesc), C.POINTER(C.c_void_p)], C.c_int),
+    "rms_run_range": ([C.c_void_p, C.POINTER(RunDesc), C.POINTER(RunState), C.c_int64, C.POINTER(C.c_void_p)],
+                      C.c_int),
     "rms_run_query": ([C.c_void_p], C.c_int),
     "rms_cancel": ([C.c_void_p], C.c_int),
     "rms_read_signal": ([C.c_void_p] + [C.c_void_p] * 4, C.c_int),

@@ -189,7 +189,9 @@ def rms_sequence_bvalues(seq: Sequence) -> np.ndarray:
 
 def rms_run(seq: Sequence, n_walkers: int, seed: int, precision: int = RMS_FP64, flags: int = 0,
             walker_begin: int = 0, steps_per_launch: int = 0, stream: Optional[int] = None,
-            interaction: int = RMS_EC) -> Run:
+            interaction: int = RMS_EC, resume: Optional[dict] = None, step_end: int = 0) -> Run:
+    """rms_run, or rms_run_range when `resume` (a state: `step` plus the arrays
+    rms_read_walkers returns and optionally `moments`) or `step_end` is given."""
     d = L.RunDesc()
     d.n_walkers = int(n_walkers)
     d.walker_begin = int(walker_begin)
@@ -200,7 +202,24 @@ def rms_run(seq: Sequence, n_walkers: int, seed: int, precision: int = RMS_FP64,
     d.interaction = int(interaction)
     d.stream = current_stream() if stream is None else stream
     h = C.c_void_p()
-    check(L.lib.rms_run(seq.handle, C.byref(d), C.byref(h)))
+    if resume is None and not step_end:
+        check(L.lib.rms_run(seq.handle, C.byref(d), C.byref(h)))
+    else:
+        keep = []
+        st = None
+        if resume is not None:
+            st = L.RunState()
+            st.step = int(resume["step"])
+            for name, dt in (("i", np.int32), ("o", np.float64), ("i0", np.int32), ("o0", np.float64),
+                             ("c", np.int32), ("A", np.float64), ("phase", np.float64), ("hash", np.uint64),
+                             ("moments", np.float64)):
+                a = resume.get(name)
+                if a is not None:
+                    a = np.ascontiguousarray(a, dtype=dt)
+                    keep.append(a)
+                    setattr(st, name, a.ctypes.data)
+        check(L.lib.rms_run_range(seq.handle, C.byref(d), C.byref(st) if st is not None else None, int(step_end),
+                                  C.byref(h)))
     return Run(h, seq, int(n_walkers), precision, flags, int(interaction))
 
 
@@ -257,10 +276,14 @@ def rms_destroy_substrate(sub: Substrate) -> None:
 
 def simulate(wl, precision: int = RMS_FP64, n_walkers: Optional[int] = None, seed: Optional[int] = None,
              hash_: bool = False, walker_begin: int = 0, steps_per_launch: int = 0, walkers: bool = False,
-             stream: Optional[int] = None, interaction: Optional[int] = None, checked: bool = False) -> dict:
+             stream: Optional[int] = None, interaction: Optional[int] = None, checked: bool = False,
+             resume: Optional[dict] = None, step_end: int = 0) -> dict:
     """Run one workload (an rms_inputs.Workload) end to end through the C ABI.
     The interaction defaults to the workload's (elastic collision if unset);
-    `leap_limit` in the result is True when an ERL step used up its draws."""
+    `leap_limit` in the result is True when an ERL step used up its draws.
+    `resume` / `step_end` run part of the sequence (rms_run_range): a result
+    with walkers=True and its `moments` is a state to resume from, given the
+    number of steps it took as `step`."""
     sub = rms_create_substrate(wl.labels, wl.voxel_um, wl.D, T2=wl.T2, T1=wl.T1, kappa=wl.kappa, dead=wl.dead,
                                periodic=wl.periodic, stream=stream, rho=getattr(wl, "rho", None),
                                conc=getattr(wl, "conc", None), lam=getattr(wl, "lam", -1.0),
@@ -271,7 +294,8 @@ def simulate(wl, precision: int = RMS_FP64, n_walkers: Optional[int] = None, see
     run = rms_run(seq, wl.n_walkers if n_walkers is None else n_walkers, wl.seed if seed is None else seed,
                   precision, (RMS_TRAJ_HASH if hash_ else 0) | (RMS_CHECKED if checked else 0), walker_begin,
                   steps_per_launch, stream,
-                  int(getattr(wl, "interaction", RMS_EC)) if interaction is None else int(interaction))
+                  int(getattr(wl, "interaction", RMS_EC)) if interaction is None else int(interaction),
+                  resume=resume, step_end=step_end)
     S, mom, asum = rms_read_signal(run)
     res = dict(S=S, moments=mom, alpha_sum=asum, status=seq.status, step_ms=rms_run_step_time_ms(run),
                b_s=rms_sequence_bvalues(seq), leap_limit=run.status == L.RMS_W_LEAP_LIMIT)

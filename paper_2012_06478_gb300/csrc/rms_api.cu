@@ -707,6 +707,7 @@ static rms_status set_sequence_impl(rms_substrate *sub, const rms_sequence_desc 
     q->n_dirs = d->n_dirs;
     q->n_b = d->n_b;
     q->n_rec = d->n_rec;
+    q->rec_steps.assign(d->rec_steps, d->rec_steps + d->n_rec);
     for (int c = 0; c < L; ++c) {
         if (sub->dead[c]) continue;
         if (std::sqrt((6.0 * sub->D[c]) * d->dt_ms) >= sub->voxel_um)
@@ -1005,6 +1006,8 @@ rms_status rms::run_setup(rms_run_handle *r, bool with_cancel_and_events)
         layout_state<double>(r->st64, r->d_state, r->W, q->S, hash, false);
     const size_t nmp = (size_t)std::max(q->n_rec, 1) * r->n_blocks * kMoments;
     RMS_CUDA(cudaMallocAsync((void **)&r->d_mom_partial, sizeof(double) * nmp, s));
+    // zero: a run that ends before some recording steps reports zero sums for them
+    RMS_CUDA(cudaMemsetAsync(r->d_mom_partial, 0, sizeof(double) * nmp, s));
     RMS_CUDA(cudaMallocAsync((void **)&r->d_mom, sizeof(double) * std::max(q->n_rec, 1) * kMoments, s));
     RMS_CUDA(cudaMallocAsync((void **)&r->d_ro_partial, sizeof(double) * 2 * (size_t)(r->n_combo + 1) * r->n_chunks, s));
     RMS_CUDA(cudaMallocAsync((void **)&r->d_S, sizeof(double) * 2 * (r->n_combo + 1), s));
@@ -1020,21 +1023,125 @@ rms_status rms::run_setup(rms_run_handle *r, bool with_cancel_and_events)
     return RMS_OK;
 }
 
-static rms_status run_impl(rms_run_handle *r, int32_t spl)
+// Resume: per-walker state from host arrays (the layouts rms_read_walkers
+// writes).  The FP32 form splits each double into its float and the Kahan
+// compensation (float - double), so the compensated value is the double's
+// to within float rounding of the difference; a saturated walker (+inf)
+// keeps kSaturatedF.
+template <typename Real>
+__global__ void import_kernel(WalkerState<Real> st, int64_t W, int32_t S, const int32_t *i, const double *o,
+                              const int32_t *i0, const double *o0, const int32_t *c, const double *A,
+                              const double *phase, const uint64_t *hash)
+{
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    constexpr bool f32 = std::is_same<Real, float>::value;
+    for (int a = 0; a < 3; ++a) {
+        st.o[a][w] = (Real)o[3 * w + a];
+        st.o0[a][w] = (Real)o0[3 * w + a];
+        st.i0[a][w] = i0[3 * w + a];
+        st.di[a][w] = i[3 * w + a] - i0[3 * w + a];
+    }
+    st.c[w] = c[w];
+    const double a = A[w];
+    if constexpr (f32) {
+        if (isinf(a)) {
+            st.A[w] = kSaturatedF;
+            st.A_c[w] = 0.0f;
+        } else {
+            const float hi = (float)a;
+            st.A[w] = hi;
+            st.A_c[w] = (float)((double)hi - a);
+        }
+    } else {
+        st.A[w] = a;
+    }
+    for (int k = 0; k < S * 3; ++k) {
+        const double p = phase[(int64_t)w * S * 3 + k];
+        const int s = k / 3, ax = k % 3;
+        const int64_t at = ((int64_t)s * 3 + ax) * W + w;
+        if constexpr (f32) {
+            const float hi = (float)p;
+            st.phase[at] = hi;
+            st.phase_c[at] = (float)((double)hi - p);
+        } else {
+            st.phase[at] = p;
+        }
+    }
+    if (st.hash) st.hash[w] = hash ? hash[w] : 0ull;
+}
+
+// Upload a stored state and seed the moment partials with the sums of the
+// recording steps it has passed (into block 0's slot: the fixed-order sum
+// over blocks then returns them unchanged).
+static rms_status run_import(rms_run_handle *r, const rms_run_state *from)
+{
+    rms_sequence *q = r->seq;
+    cudaStream_t s = r->stream;
+    const int64_t W = r->W;
+    const int S = q->S;
+    int32_t *d_i = nullptr, *d_i0 = nullptr, *d_c = nullptr;
+    double *d_o = nullptr, *d_o0 = nullptr, *d_A = nullptr, *d_ph = nullptr;
+    uint64_t *d_h = nullptr;
+    RMS_TRY(upload(&d_i, from->i, (size_t)3 * W, s));
+    RMS_TRY(upload(&d_i0, from->i0, (size_t)3 * W, s));
+    RMS_TRY(upload(&d_o, from->o, (size_t)3 * W, s));
+    RMS_TRY(upload(&d_o0, from->o0, (size_t)3 * W, s));
+    RMS_TRY(upload(&d_c, from->c, (size_t)W, s));
+    RMS_TRY(upload(&d_A, from->A, (size_t)W, s));
+    RMS_TRY(upload(&d_ph, from->phase, (size_t)3 * S * W, s));
+    if (from->hash) RMS_TRY(upload(&d_h, from->hash, (size_t)W, s));
+    const unsigned nb = (unsigned)((W + 255) / 256);
+    if (r->precision == RMS_FP32)
+        import_kernel<float><<<nb, 256, 0, s>>>(r->st32, W, S, d_i, d_o, d_i0, d_o0, d_c, d_A, d_ph, d_h);
+    else
+        import_kernel<double><<<nb, 256, 0, s>>>(r->st64, W, S, d_i, d_o, d_i0, d_o0, d_c, d_A, d_ph, d_h);
+    RMS_CUDA(cudaGetLastError());
+    if (from->moments)
+        for (int rr = 0; rr < q->n_rec; ++rr)
+            if (q->rec_steps[rr] <= from->step)
+                RMS_CUDA(cudaMemcpyAsync(r->d_mom_partial + (size_t)rr * r->n_blocks * kMoments, from->moments + 22 * rr,
+                                         sizeof(double) * kMoments, cudaMemcpyHostToDevice, s));
+    void *tmp[] = {d_i, d_i0, d_c, d_o, d_o0, d_A, d_ph, d_h};
+    for (void *x : tmp)
+        if (x) RMS_CUDA(cudaFreeAsync(x, s));
+    RMS_CUDA(cudaStreamSynchronize(s));  // the host arrays may go once this returns
+    return RMS_OK;
+}
+
+// Set up, then initialise (or resume) and enqueue steps (k_first, k_last].
+static rms_status run_impl(rms_run_handle *r, int32_t spl, const rms_run_state *from, int64_t k_first,
+                           int64_t k_last)
 {
     RMS_TRY(run_setup(r, true));
-    RMS_TRY(run_init(r));
+    if (from)
+        RMS_TRY(run_import(r, from));
+    else
+        RMS_TRY(run_init(r));
     RMS_CUDA(cudaEventRecord(r->ev_start, r->stream));
-    for (int64_t k0 = 0; k0 < r->seq->n_steps; k0 += spl)
-        RMS_TRY(run_walk(r, k0, std::min<int64_t>(r->seq->n_steps, k0 + spl)));
+    for (int64_t k0 = k_first; k0 < k_last; k0 += spl)
+        RMS_TRY(run_walk(r, k0, std::min<int64_t>(k_last, k0 + spl)));
     RMS_CUDA(cudaEventRecord(r->ev_end, r->stream));
     return run_finalize(r);
 }
 
 extern "C" rms_status rms_run(rms_sequence *q, const rms_run_desc *d, rms_run_handle **out)
 {
+    return rms_run_range(q, d, nullptr, 0, out);
+}
+
+extern "C" rms_status rms_run_range(rms_sequence *q, const rms_run_desc *d, const rms_run_state *from,
+                                    int64_t step_end, rms_run_handle **out)
+{
     if (!q || !d || !out) return fail(RMS_E_INVALID_ARG, "null argument");
     *out = nullptr;
+    const int64_t k_first = from ? from->step : 0;
+    const int64_t k_last = step_end > 0 ? step_end : q->n_steps;
+    if (from && (!from->i || !from->o || !from->i0 || !from->o0 || !from->c || !from->A ||
+                 (q->S > 0 && !from->phase)))
+        return fail(RMS_E_INVALID_ARG, "resume state: null array");
+    if (k_first < 0 || k_first > k_last || k_last > q->n_steps || step_end < 0)
+        return fail(RMS_E_INVALID_ARG, "need 0 <= from->step <= step_end <= n_steps (step_end 0: n_steps)");
     if (d->n_walkers < 1 || d->n_walkers > (1ll << 31) - 1 || d->walker_begin < 0)
         return fail(RMS_E_INVALID_ARG, "n_walkers must be in [1, 2^31) and walker_begin >= 0");
     if (d->precision != RMS_FP64 && d->precision != RMS_FP32)
@@ -1058,7 +1165,7 @@ extern "C" rms_status rms_run(rms_sequence *q, const rms_run_desc *d, rms_run_ha
         const int64_t target = 2000000000ll / std::max<int64_t>(r->W, 1);
         spl = (int32_t)std::max<int64_t>(64, std::min<int64_t>(target, std::max<int64_t>(q->n_steps, 1)));
     }
-    rms_status st = run_impl(r, spl);
+    rms_status st = run_impl(r, spl, from, k_first, k_last);
     if (st < 0) {
         run_free(r, true);
         delete r;

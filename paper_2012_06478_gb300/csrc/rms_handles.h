@@ -39,6 +39,7 @@ struct rms_sequence {
     int32_t S = 0, n_dirs = 0, n_b = 0, n_rec = 0;
     int32_t any_relax = 0;
     int32_t has_mode = 0;
+    std::vector<int64_t> rec_steps;  // host copy of the recording steps
     double *d_s64 = nullptr, *d_dtR64 = nullptr, *d_wG64 = nullptr;
     float *d_s32 = nullptr, *d_dtR32 = nullptr, *d_wG32 = nullptr;
     uint32_t *d_T = nullptr;
