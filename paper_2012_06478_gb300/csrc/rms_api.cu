@@ -503,6 +503,7 @@ static rms_status concentration_tables(rms_substrate *s, int64_t nvox, cudaStrea
 
 static rms_status create_substrate_impl(const rms_substrate_desc *d, rms_substrate *s)
 {
+    NvtxRange range("rms: substrate upload and tables");
     cudaStream_t st = (cudaStream_t)d->stream;
     const int64_t nvox = (int64_t)d->nx * d->ny * d->nz;
     const int L = d->n_labels;
@@ -696,6 +697,7 @@ static void free_sequence(rms_sequence *q, cudaStream_t st)
 static rms_status set_sequence_impl(rms_substrate *sub, const rms_sequence_desc *d, rms_sequence *q,
                                     bool *warn)
 {
+    NvtxRange range("rms: sequence tables");
     cudaStream_t st = 0;
     const int L = sub->L;
     const int64_t N = d->n_steps;
@@ -930,6 +932,7 @@ static rms_status walk_impl(rms_run_handle *r, int64_t k0, int64_t k1)
 
 rms_status rms::run_walk(rms_run_handle *r, int64_t k0, int64_t k1)
 {
+    NvtxRange range("rms: walk slice");
     return r->precision == RMS_FP32 ? walk_impl<float>(r, k0, k1) : walk_impl<double>(r, k0, k1);
 }
 
@@ -957,6 +960,7 @@ static rms_status finalize_impl(rms_run_handle *r)
 
 rms_status rms::run_finalize(rms_run_handle *r)
 {
+    NvtxRange range("rms: moments and read-out");
     return r->precision == RMS_FP32 ? finalize_impl<float>(r) : finalize_impl<double>(r);
 }
 
@@ -1113,6 +1117,7 @@ static rms_status run_import(rms_run_handle *r, const rms_run_state *from)
 static rms_status run_impl(rms_run_handle *r, int32_t spl, const rms_run_state *from, int64_t k_first,
                            int64_t k_last)
 {
+    NvtxRange range("rms: run");
     RMS_TRY(run_setup(r, true));
     if (from)
         RMS_TRY(run_import(r, from));

@@ -8,8 +8,19 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/rms.h"
 #include "rms_device.cuh"
+
+// A host-side NVTX range for the lifetime of the object (header-only NVTX
+// v3: no link dependency, and a no-op unless a profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct rms_substrate {
     int device = 0;

@@ -218,6 +218,7 @@ void admit(rms_server *s)
 // One tick: every active request advances by up to steps_per_tick steps.
 rms_status tick_once(rms_server *s)
 {
+    NvtxRange nvtx_range("rms: serving tick");
     const int j = (int)(s->tick & 1);
     RMS_CUDA(cudaEventSynchronize(s->buf_ev[j]));  // the upload from buffer j has run
     // drop cancelled requests from the active set (their memory is released

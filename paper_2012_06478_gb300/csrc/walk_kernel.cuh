@@ -131,6 +131,15 @@ __device__ __forceinline__ void saturate(float &A, float &Ac)
     Ac = 0.0f;
 }
 
+// Word 0 of a step's PERM call: the Bernoulli word of a third membrane event
+// in one step.  Rare, so kept out of line: inlined, the ten Philox rounds
+// would sit in every pass of the face-event loop (measured: 4 % of the FP32
+// step on the axon workload).
+static __device__ __noinline__ uint32_t perm_word(uint64_t seed, uint64_t w, uint32_t k, uint32_t call)
+{
+    return draw(seed, w, k, kTagPerm, call).x;
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -338,7 +347,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                     } else {
                         // third membrane event of a step: word 0 of the step's PERM call
                         const uint32_t word =
-                            ev == 0 ? x.z : (ev == 1 ? x.w : draw(ctl.seed, w, (uint32_t)k, kTagPerm, att).x);
+                            ev == 0 ? x.z : (ev == 1 ? x.w : perm_word(ctl.seed, w, (uint32_t)k, att));
                         cross = word < T;
                     }
                 }
