@@ -64,6 +64,9 @@ typedef int rms_status;
                             offsets in [0,1] -- in the verification kernel (the one that also keeps
                             the checksum); a violation makes the read calls return RMS_E_DEVICE.
                             Slower; for testing and debugging. */
+#define RMS_COUNTS 4u    /* count, per walker, face events, crossings into another label and
+                            reflections (or steps a refused walker stayed, RS/ERL) -- in the
+                            verification kernel; read with rms_read_counts */
 
 /* Particle-membrane interaction of rms_run (Sec. 2.1.2).  A face is "refused"
  * when it is impermeable (a label pair with kappa = 0, a dead label, the wall
@@ -273,6 +276,13 @@ rms_status rms_read_signal(rms_run_handle *run, double *S_re, double *S_im, doub
  * double, sum_k dt G_k dx_k in um ms), hash (W uint64, RMS_TRAJ_HASH runs). */
 rms_status rms_read_walkers(rms_run_handle *run, int32_t *i, double *o, int32_t *i0, double *o0, int32_t *c,
                             double *A, double *phase, uint64_t *hash);
+
+/* Wait for the run and copy its per-walker counts to host memory: W*3 int64
+ * (face events, crossings into another label, reflections -- under RS/ERL
+ * the steps a refused walker stayed), over the run's steps.  The events of
+ * a draw that a membrane refused are not counted.  RMS_E_INVALID_ARG when
+ * the run was made without RMS_COUNTS. */
+rms_status rms_read_counts(rms_run_handle *run, int64_t *counts);
 
 /* Free the run (waits for it first). */
 rms_status rms_destroy_run(rms_run_handle *run);

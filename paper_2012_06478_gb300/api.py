@@ -17,14 +17,13 @@ from typing import Optional, Sequence as Seq
 import numpy as np
 
 from . import _lib as L
-from ._lib import RMS_CHECKED, RMS_EC, RMS_ERL, RMS_FP32, RMS_FP64, RMS_RS, RMS_TRAJ_HASH, RmsError, check
+from ._lib import RMS_CHECKED, RMS_COUNTS, RMS_EC, RMS_ERL, RMS_FP32, RMS_FP64, RMS_RS, RMS_TRAJ_HASH, RmsError, check
 
 __all__ = ["rms_create_substrate", "rms_set_sequence", "rms_run", "rms_read_signal", "rms_read_walkers",
-           "rms_cancel", "rms_run_query", "rms_destroy_run", "rms_destroy_sequence", "rms_destroy_substrate",
-           "rms_sequence_bvalues", "rms_run_step_time_ms", "simulate", "current_stream",
-           "RMS_FP32", "RMS_FP64", "RMS_TRAJ_HASH", "RMS_CHECKED", "RMS_EC", "RMS_RS", "RMS_ERL", "RmsError",
-           "MOMENT_NAMES",
-           "Server"]
+           "rms_read_counts", "rms_cancel", "rms_run_query", "rms_destroy_run", "rms_destroy_sequence",
+           "rms_destroy_substrate", "rms_sequence_bvalues", "rms_run_step_time_ms", "simulate", "current_stream",
+           "RMS_FP32", "RMS_FP64", "RMS_TRAJ_HASH", "RMS_CHECKED", "RMS_COUNTS", "RMS_EC", "RMS_RS", "RMS_ERL",
+           "RmsError", "MOMENT_NAMES", "Server"]
 
 MOMENT_NAMES = ["1", "xx", "xy", "xz", "yy", "yz", "zz", "xxxx", "xxxy", "xxxz", "xxyy", "xxyz", "xxzz", "xyyy",
                 "xyyz", "xyzz", "xzzz", "yyyy", "yyyz", "yyzz", "yzzz", "zzzz"]
@@ -256,6 +255,14 @@ def rms_read_walkers(run: Run) -> dict:
     return out
 
 
+def rms_read_counts(run: Run) -> np.ndarray:
+    """(W, 3) int64: face events, crossings into another label, reflections
+    (or RS/ERL stays) per walker; the run needs RMS_COUNTS."""
+    out = np.zeros((run.n_walkers, 3), np.int64)
+    run.status = check(L.lib.rms_read_counts(run.handle, out.ctypes.data), allow=(L.RMS_OK, L.RMS_W_LEAP_LIMIT))
+    return out
+
+
 def rms_run_step_time_ms(run: Run) -> float:
     ms = C.c_float()
     check(L.lib.rms_run_step_time_ms(run.handle, C.byref(ms)))
@@ -277,7 +284,7 @@ def rms_destroy_substrate(sub: Substrate) -> None:
 def simulate(wl, precision: int = RMS_FP64, n_walkers: Optional[int] = None, seed: Optional[int] = None,
              hash_: bool = False, walker_begin: int = 0, steps_per_launch: int = 0, walkers: bool = False,
              stream: Optional[int] = None, interaction: Optional[int] = None, checked: bool = False,
-             resume: Optional[dict] = None, step_end: int = 0) -> dict:
+             resume: Optional[dict] = None, step_end: int = 0, counts: bool = False) -> dict:
     """Run one workload (an rms_inputs.Workload) end to end through the C ABI.
     The interaction defaults to the workload's (elastic collision if unset);
     `leap_limit` in the result is True when an ERL step used up its draws.
@@ -292,7 +299,9 @@ def simulate(wl, precision: int = RMS_FP64, n_walkers: Optional[int] = None, see
     G = G.reshape(-1, wl.n_steps) if wl.n_steps else np.zeros((G.shape[0] if G.ndim == 2 else 1, 0))
     seq = rms_set_sequence(sub, wl.dt, G, wl.dirs, wl.b, wl.rec_steps, mode=wl.mode)
     run = rms_run(seq, wl.n_walkers if n_walkers is None else n_walkers, wl.seed if seed is None else seed,
-                  precision, (RMS_TRAJ_HASH if hash_ else 0) | (RMS_CHECKED if checked else 0), walker_begin,
+                  precision,
+                  (RMS_TRAJ_HASH if hash_ else 0) | (RMS_CHECKED if checked else 0) | (RMS_COUNTS if counts else 0),
+                  walker_begin,
                   steps_per_launch, stream,
                   int(getattr(wl, "interaction", RMS_EC)) if interaction is None else int(interaction),
                   resume=resume, step_end=step_end)
@@ -301,6 +310,8 @@ def simulate(wl, precision: int = RMS_FP64, n_walkers: Optional[int] = None, see
                b_s=rms_sequence_bvalues(seq), leap_limit=run.status == L.RMS_W_LEAP_LIMIT)
     if walkers:
         res.update(rms_read_walkers(run))
+    if counts:
+        res["counts"] = rms_read_counts(run)
     run.close()
     seq.close()
     sub.close()

@@ -306,6 +306,8 @@ __global__ void init_kernel(Geometry g, const int32_t *ok_list, int64_t n_ok, co
         if (st.phase_c) st.phase_c[(int64_t)k * ctl.n_walkers + li] = Real(0);
     }
     if (hash) st.hash[li] = 0ull;
+    if (st.counts)
+        for (int a = 0; a < 3; ++a) st.counts[(int64_t)a * ctl.n_walkers + li] = 0;
 }
 
 // ------------------------------------------------------------------ reductions
@@ -836,7 +838,7 @@ extern "C" rms_status rms_destroy_sequence(rms_sequence *q)
 // ------------------------------------------------------------------ run
 
 template <typename Real>
-size_t rms::layout_state(WalkerState<Real> &st, char *base, int64_t W, int S, bool hash, bool f32)
+size_t rms::layout_state(WalkerState<Real> &st, char *base, int64_t W, int S, bool hash, bool f32, bool counts)
 {
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -854,6 +856,7 @@ size_t rms::layout_state(WalkerState<Real> &st, char *base, int64_t W, int S, bo
     st.phase = (Real *)take(sizeof(Real) * W * S * 3);
     st.phase_c = f32 ? (Real *)take(sizeof(Real) * W * S * 3) : nullptr;
     st.hash = hash ? (uint64_t *)take(sizeof(uint64_t) * W) : nullptr;
+    st.counts = counts ? (int32_t *)take(sizeof(int32_t) * 3 * W) : nullptr;
     return off;
 }
 
@@ -896,7 +899,7 @@ static rms_status init_impl(rms_run_handle *r)
     const ReqDesc<Real> d = run_desc<Real>(r);
     const unsigned ib = (unsigned)((r->W + 255) / 256);
     init_kernel<Real><<<ib, 256, 0, r->stream>>>(d.g, r->seq->sub->d_ok, r->seq->sub->n_ok, r->seq->sub->d_acc, d.st,
-                                                  d.ctl, (r->flags & (RMS_TRAJ_HASH | RMS_CHECKED)) != 0);
+                                                  d.ctl, (r->flags & kVerifyFlags) != 0);
     RMS_CUDA(cudaGetLastError());
     return RMS_OK;
 }
@@ -910,7 +913,7 @@ template <typename Real>
 static rms_status walk_impl(rms_run_handle *r, int64_t k0, int64_t k1)
 {
     const ReqDesc<Real> d = run_desc<Real>(r);
-    const bool hash = (r->flags & (RMS_TRAJ_HASH | RMS_CHECKED)) != 0;  // the verification kernel
+    const bool hash = (r->flags & kVerifyFlags) != 0;  // the verification kernel
     const dim3 grid((unsigned)r->n_blocks);
     const int S = r->seq->S;
 #define RMS_WALK(IM, MT) \
@@ -980,12 +983,13 @@ size_t rms::run_state_bytes(const rms_sequence *q, int64_t W, int32_t precision,
 {
     WalkerState<double> s64{};
     WalkerState<float> s32{};
-    const bool hash = (flags & (RMS_TRAJ_HASH | RMS_CHECKED)) != 0;
+    const bool hash = (flags & kVerifyFlags) != 0;
     const int64_t nb = (W + kWalkBlockSize - 1) / kWalkBlockSize;
     const int64_t nc = (W + kRoChunk - 1) / kRoChunk;
     const int64_t ncombo = (int64_t)q->S * q->n_dirs * q->n_b;
-    size_t b = precision == RMS_FP32 ? layout_state<float>(s32, nullptr, W, q->S, hash, true)
-                                     : layout_state<double>(s64, nullptr, W, q->S, hash, false);
+    const bool cnt = (flags & RMS_COUNTS) != 0;
+    size_t b = precision == RMS_FP32 ? layout_state<float>(s32, nullptr, W, q->S, hash, true, cnt)
+                                     : layout_state<double>(s64, nullptr, W, q->S, hash, false, cnt);
     b += sizeof(double) * ((size_t)std::max(q->n_rec, 1) * nb * kMoments + (size_t)std::max(q->n_rec, 1) * kMoments +
                            2 * (size_t)(ncombo + 1) * nc + 2 * (size_t)(ncombo + 1));
     return b;
@@ -996,18 +1000,19 @@ rms_status rms::run_setup(rms_run_handle *r, bool with_cancel_and_events)
 {
     rms_sequence *q = r->seq;
     cudaStream_t s = r->stream;
-    const bool hash = (r->flags & (RMS_TRAJ_HASH | RMS_CHECKED)) != 0;
+    const bool hash = (r->flags & kVerifyFlags) != 0;
     const bool f32 = r->precision == RMS_FP32;
     r->n_blocks = (int32_t)((r->W + walk_block_size() - 1) / walk_block_size());
     r->n_combo = q->S * q->n_dirs * q->n_b;
     r->n_chunks = (int32_t)((r->W + kRoChunk - 1) / kRoChunk);
-    const size_t bytes = f32 ? layout_state<float>(r->st32, nullptr, r->W, q->S, hash, true)
-                             : layout_state<double>(r->st64, nullptr, r->W, q->S, hash, false);
+    const bool cnt = (r->flags & RMS_COUNTS) != 0;
+    const size_t bytes = f32 ? layout_state<float>(r->st32, nullptr, r->W, q->S, hash, true, cnt)
+                             : layout_state<double>(r->st64, nullptr, r->W, q->S, hash, false, cnt);
     RMS_CUDA(cudaMallocAsync((void **)&r->d_state, bytes, s));
     if (f32)
-        layout_state<float>(r->st32, r->d_state, r->W, q->S, hash, true);
+        layout_state<float>(r->st32, r->d_state, r->W, q->S, hash, true, cnt);
     else
-        layout_state<double>(r->st64, r->d_state, r->W, q->S, hash, false);
+        layout_state<double>(r->st64, r->d_state, r->W, q->S, hash, false, cnt);
     const size_t nmp = (size_t)std::max(q->n_rec, 1) * r->n_blocks * kMoments;
     RMS_CUDA(cudaMallocAsync((void **)&r->d_mom_partial, sizeof(double) * nmp, s));
     // zero: a run that ends before some recording steps reports zero sums for them
@@ -1073,6 +1078,8 @@ __global__ void import_kernel(WalkerState<Real> st, int64_t W, int32_t S, const 
         }
     }
     if (st.hash) st.hash[w] = hash ? hash[w] : 0ull;
+    if (st.counts)
+        for (int k = 0; k < 3; ++k) st.counts[(int64_t)k * W + w] = 0;
 }
 
 // Upload a stored state and seed the moment partials with the sums of the
@@ -1151,7 +1158,7 @@ extern "C" rms_status rms_run_range(rms_sequence *q, const rms_run_desc *d, cons
         return fail(RMS_E_INVALID_ARG, "n_walkers must be in [1, 2^31) and walker_begin >= 0");
     if (d->precision != RMS_FP64 && d->precision != RMS_FP32)
         return fail(RMS_E_INVALID_ARG, "precision must be RMS_FP64 or RMS_FP32");
-    if (d->flags & ~(RMS_TRAJ_HASH | RMS_CHECKED)) return fail(RMS_E_INVALID_ARG, "unknown flag");
+    if (d->flags & ~kVerifyFlags) return fail(RMS_E_INVALID_ARG, "unknown flag");
     if (d->steps_per_launch < 0) return fail(RMS_E_INVALID_ARG, "steps_per_launch must be >= 0");
     if (d->interaction != RMS_EC && d->interaction != RMS_RS && d->interaction != RMS_ERL)
         return fail(RMS_E_INVALID_ARG, "interaction must be RMS_EC, RMS_RS or RMS_ERL");
@@ -1258,7 +1265,7 @@ extern "C" rms_status rms_read_walkers(rms_run_handle *r, int32_t *i, double *o,
     double *dp = (double *)(buf + offs[6]);
     uint64_t *dh = (uint64_t *)(buf + offs[7]);
     const unsigned nb = (unsigned)((W + 255) / 256);
-    const bool hsh = (r->flags & (RMS_TRAJ_HASH | RMS_CHECKED)) != 0;
+    const bool hsh = (r->flags & kVerifyFlags) != 0;
     if (r->precision == RMS_FP32)
         export_kernel<float><<<nb, 256, 0, s>>>(r->st32, W, S, hsh, di, dO, di0, dO0, dc, dA, dp, dh);
     else
@@ -1274,6 +1281,20 @@ extern "C" rms_status rms_read_walkers(rms_run_handle *r, int32_t *i, double *o,
         if (x.h) RMS_CUDA(cudaMemcpyAsync(x.h, x.d, x.n, cudaMemcpyDeviceToHost, s));
     RMS_CUDA(cudaFreeAsync(buf, s));
     RMS_CUDA(cudaStreamSynchronize(s));
+    return fin;
+}
+
+extern "C" rms_status rms_read_counts(rms_run_handle *r, int64_t *counts)
+{
+    if (!r || !counts) return fail(RMS_E_INVALID_ARG, "null argument");
+    const rms_status fin = finish(r);
+    if (fin < 0) return fin;
+    const int32_t *d = r->precision == RMS_FP32 ? r->st32.counts : r->st64.counts;
+    if (!d) return fail(RMS_E_INVALID_ARG, "the run was made without RMS_COUNTS");
+    std::vector<int32_t> h((size_t)3 * r->W);
+    RMS_CUDA(cudaMemcpy(h.data(), d, sizeof(int32_t) * h.size(), cudaMemcpyDeviceToHost));
+    for (int64_t w = 0; w < r->W; ++w)
+        for (int a = 0; a < 3; ++a) counts[3 * w + a] = h[(size_t)a * r->W + w];
     return fin;
 }
 

@@ -110,6 +110,7 @@ struct WalkerState {
     Real *phase;       // [shape][axis][W]
     Real *phase_c;     // Kahan compensation (FP32 form only), same layout
     uint64_t *hash;
+    int32_t *counts;   // [3][W]: face events, crossings, reflections (RMS_COUNTS) or nullptr
 };
 
 struct Geometry {

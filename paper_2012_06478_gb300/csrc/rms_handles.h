@@ -103,7 +103,10 @@ rms_status fail(rms_status st, const std::string &msg);
     } while (0)
 
 template <typename Real>
-size_t layout_state(WalkerState<Real> &st, char *base, int64_t W, int S, bool hash, bool f32);
+size_t layout_state(WalkerState<Real> &st, char *base, int64_t W, int S, bool hash, bool f32, bool counts);
+
+// Run flags that select the verification kernel (checksum, invariant checks, counts).
+constexpr uint32_t kVerifyFlags = RMS_TRAJ_HASH | RMS_CHECKED | RMS_COUNTS;
 
 // Stages of a run, each enqueued on r->stream.
 rms_status run_setup(rms_run_handle *r, bool with_cancel_and_events);  // allocate, lay out

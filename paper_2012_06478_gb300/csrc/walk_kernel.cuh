@@ -222,6 +222,8 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
     Real A = Real(0), Ac = Real(0);
     Real ph[NS][3], phc[NS][3];
     uint64_t h = 0;
+    // face events, crossings into another label, reflections (verification kernel)
+    [[maybe_unused]] int32_t nev = 0, ncr = 0, nrf = 0;
     if (active) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -245,6 +247,13 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                                 : Real(0);
             }
         if (HASH) h = st.hash[li];
+        if constexpr (HASH) {
+            if (st.counts) {
+                nev = st.counts[li];
+                ncr = st.counts[ctl.n_walkers + li];
+                nrf = st.counts[2 * ctl.n_walkers + li];
+            }
+        }
     } else {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -263,7 +272,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
             const int mode = t.mode ? (int)__ldg(t.mode + (k - 1)) : 0;
             // state at the step start, restored when a membrane refuses the step
             [[maybe_unused]] Real o_s[3], A_s, Ac_s;
-            [[maybe_unused]] int32_t wc_s[3], di_s[3], v_s, c_s;
+            [[maybe_unused]] int32_t wc_s[3], di_s[3], v_s, c_s, nev_s, ncr_s, nrf_s;
             if constexpr (IM != kInteractEC) {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
@@ -275,6 +284,11 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                 c_s = c;
                 A_s = A;
                 Ac_s = Ac;
+                if constexpr (HASH) {
+                    nev_s = nev;
+                    ncr_s = ncr;
+                    nrf_s = nrf;
+                }
             }
             uint32_t att = 0;  // draw index (ERL redraws); always 0 otherwise
             [[maybe_unused]] bool sat_any = false;  // saturated on some draw of this step (MT)
@@ -361,6 +375,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                         }
                     v = nv;
                     if (c2 != c) {
+                        if constexpr (HASH) ++ncr;
                         c = c2;
                         if (t.any_relax) rate = __ldg(t.dtR + mode * L + c);
                         return true;  // the caller switches to the new label's step length
@@ -368,6 +383,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                 } else if constexpr (IM != kInteractEC) {
                     refused = true;
                 } else {
+                    if constexpr (HASH) ++nrf;
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
                         if (a == best) {
@@ -424,6 +440,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                     }
                     if (t.any_relax) A = A + dts * rate;
                     tau = tmin;
+                    if constexpr (HASH) ++nev;
                     const bool changed = face(best, up, ev);
                     if constexpr (IM != kInteractEC) {
                         if (refused) break;
@@ -486,6 +503,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                     }
                     if (t.any_relax) kahan_add(A, Ac, dtt * rate);
                     tau = tmin;
+                    if constexpr (HASH) ++nev;
                     const bool changed = face(best, up, ev);
                     if constexpr (IM != kInteractEC) {
                         if (refused) break;
@@ -526,6 +544,11 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                 c = c_s;
                 A = A_s;
                 Ac = Ac_s;
+                if constexpr (HASH) {
+                    nev = nev_s;
+                    ncr = ncr_s;
+                    nrf = nrf_s;
+                }
                 if constexpr (MT) {
                     if (sat_any) saturate(A, Ac);  // a saturation met on a cancelled draw stays
                 }
@@ -538,6 +561,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                             kahan_add(A, Ac, rate0);
                     }
                     if (IM == kInteractERL) atomicOr(ctl.status, kWarnLeaps);
+                    if constexpr (HASH) ++nrf;
                     break;
                 }
             }
@@ -619,6 +643,13 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                     if (!kF64) st.phase_c[((int64_t)s * 3 + a) * ctl.n_walkers + li] = phc[s][a];
                 }
         if (HASH) st.hash[li] = h;
+        if constexpr (HASH) {
+            if (st.counts) {
+                st.counts[li] = nev;
+                st.counts[ctl.n_walkers + li] = ncr;
+                st.counts[2 * ctl.n_walkers + li] = nrf;
+            }
+        }
     }
 }
 
