@@ -11,7 +11,10 @@
  * probability of Eq. 3 or are reflected specularly (Sec. 2.1.3), accumulate
  * the phase of Eq. 7 and the relaxation weight of Eq. 5, and are reduced to
  * the signal S(b, g) (Eq. 7) and the displacement moments behind the
- * narrow-pulse D(t) and K(t) (Sec. 2.3).
+ * narrow-pulse D(t) and K(t) (Sec. 2.3).  It also runs the alternatives the
+ * paper analyses: rejection sampling and the equal-step-length random leap
+ * (App. A-B), absorbing membranes for magnetization transfer (Sec. 2.1.3),
+ * spin concentrations and Baxter's permeation rule (App. C.2-C.3).
  *
  * Conventions for every call:
  *   - Plain C types and pointers only.  "host pointer" = ordinary process

@@ -28,6 +28,10 @@
  *     for relaxation); the equal-step-length random leap (ERL) cancels it and
  *     draws a new direction until a step is admitted (at most 64 draws, then
  *     the walker stays and an error bit is set).
+ *   - App. C.2-C.3: spin concentrations c per label -- the generalised Eq. 3
+ *     with (c2/c1)^lambda factors and its finite-step correction, walkers
+ *     starting with density proportional to c -- and Baxter's rule
+ *     P_{1->2} = c2 sqrt(D2) / (c1 sqrt(D1)) (at most 1).
  *
  * The paper does not print its kernel; the step is taken here in the order
  * and notation of Sec. 2.2, with every point where the text is silent fixed
