@@ -352,7 +352,8 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if hbm else None, "traffic": prof.get("traffic_per_launch"),
-                     "kernel": f"walk_kernel<float,1,false,{INTERACTIONS[args.interaction]}>",
+                     "kernel": f"walk_kernel<float,1,false,{INTERACTIONS[args.interaction]},"
+                               f"{'true' if args.rho > 0 else 'false'}>",
                      "alg_bytes_per_walker_step": 2.0 * eps,
                      "walker_steps_per_launch": W * spl, "launch_ms": walk_launch_ms,
                      "what": "label-lookup bytes (2 B per face event) against HBM copy bandwidth (of measured)"},
