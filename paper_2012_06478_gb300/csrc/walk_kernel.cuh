@@ -2,14 +2,17 @@
 // Lee, Fieremans & Novikov, arXiv 2012.06478), templated on the arithmetic
 // type.  Included by walk_fp64.cu (built without FMA contraction: the plain
 // form reproduces the CPU FP64 reference bit for bit) and walk_fp32.cu (the
-// precision form: voxel index + FP32 offset, FP32 Kahan-compensated phase).
+// precision form: voxel index + FP32 offset, FP32 Kahan-compensated phase),
+// and by walk_reject_fp{64,32}.cu and walk_mt_fp{64,32}.cu for the other
+// particle-membrane interactions and for absorbing membranes.
 //
 // One thread owns one walker for a slice of steps; its whole state stays in
 // registers for the slice and goes back to global memory (structure of
 // arrays, coalesced) at the end.  Per step and walker the only memory
 // traffic is the dependent 2-byte label gather across each face met
 // (Sec. 2.1.1: the label volume is the lookup table), the threshold of the
-// label pair at a membrane, and warp-uniform broadcasts of the waveform.
+// label pair at a membrane (and its saturation threshold, with absorbing
+// membranes), and warp-uniform broadcasts of the waveform.
 #pragma once
 
 #include <cstdint>
