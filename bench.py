@@ -390,7 +390,7 @@ def main():
 # thread_inst_executed_per_inst_executed / walker-steps) and DRAM bytes read +
 # written per launch.  Workloads without a capture report null.
 PROFILED = {
-    "axons-200x200x400": {"inst_per_walker_step": 324.8, "traffic_per_launch": 152.2e6,
+    "axons-200x200x400": {"inst_per_walker_step": 302.8, "traffic_per_launch": 152.4e6,
                           "profile": "profiles/walk_kernel_fp32_axons-200x200x400.md"},
 }
 ISSUE_LANES_PER_CLOCK = 152 * 4 * 32  # SMs x schedulers x lanes

