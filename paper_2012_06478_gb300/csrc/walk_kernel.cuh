@@ -83,13 +83,50 @@ __device__ __forceinline__ void octant_map(uint32_t oct, double cs, double sn, d
     sy = negy ? -b : b;
 }
 
+// Exact doubles built from their bits on the integer ALU, so that values
+// which need no rounding do not occupy GB300's narrow FP64 pipe.
+// k * 2^e2 for an odd |k| < 2^32: no rounding, the same bits as converting k
+// and multiplying by the power of two.
+__device__ __forceinline__ double odd_scaled(uint32_t mag, bool neg, int e2)
+{
+    const int p = 31 - __clz((int)mag);  // position of the leading one
+    const unsigned long long mant = ((unsigned long long)mag << (52 - p)) & 0x000FFFFFFFFFFFFFULL;
+    const unsigned long long bits = (neg ? 0x8000000000000000ULL : 0ULL) |
+                                    ((unsigned long long)(p + e2 + 1023) << 52) | mant;
+    return __longlong_as_double((long long)bits);
+}
+// N 2^-64 rounded to the nearest double, ties to even (0 < N < 2^64): the
+// IEEE result of a product of doubles whose exact value is N 2^-64.
+__device__ __forceinline__ double u64_scaled_rn(unsigned long long N)
+{
+    const int p = 63 - __clzll((long long)N);
+    int e = p - 64;
+    unsigned long long q;
+    if (p <= 52) {
+        q = N << (52 - p);
+    } else {
+        const int sh = p - 52;
+        q = N >> sh;
+        const unsigned long long rem = N & ((1ULL << sh) - 1ULL), half = 1ULL << (sh - 1);
+        if (rem > half || (rem == half && (q & 1ULL))) ++q;
+        if (q >> 53) {
+            q >>= 1;
+            ++e;
+        }
+    }
+    return __longlong_as_double((long long)(((unsigned long long)(e + 1023) << 52) | (q & 0x000FFFFFFFFFFFFFULL)));
+}
+
 __device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, const double *__restrict__ trig,
                                                double n[3])
 {
-    // z = 1 - 2 u(x0) = (2^32 - 1 - 2 x0) 2^-32: an exact integer scaled by a
-    // power of two, the same bits as the reference's step-by-step evaluation.
-    const double z = (double)(0xFFFFFFFFLL - 2LL * (long long)x0) * 0x1p-32;
-    const double r = sqrt((1.0 - z) * (1.0 + z));
+    // z = 1 - 2 u(x0) = k 2^-32 with the odd integer k = 2^32 - 1 - 2 x0, and
+    // (1 - z)(1 + z) = (2^64 - k^2) 2^-64 rounded once: both from integers,
+    // the same bits as the reference's step-by-step evaluation.
+    const bool zneg = x0 >= 0x80000000u;
+    const uint32_t kmag = zneg ? 2u * x0 + 1u : 0xFFFFFFFFu - 2u * x0;  // |k|
+    const double z = odd_scaled(kmag, zneg, -32);
+    const double r = sqrt(u64_scaled_rn(0ULL - (unsigned long long)kmag * kmag));
     const uint32_t oct = x1 >> 29;
     uint32_t m = x1 & 0x1FFFFFFFu;
     if (oct & 1u) m = 0x1FFFFFFFu - m;
@@ -97,7 +134,8 @@ __device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, const d
     // centre of part j = top 10 bits of m, |e| <= 2^-11 pi/4
     const uint32_t j = m >> 19;
     const int32_t lo = (int32_t)(m & 0x7FFFFu);
-    const double e = ((double)(2 * lo + 1 - (1 << 19)) * 0x1p-30) * 0.78539816339744830962;
+    const int32_t e_int = 2 * lo + 1 - (1 << 19);  // odd
+    const double e = odd_scaled((uint32_t)(e_int < 0 ? -e_int : e_int), e_int < 0, -30) * 0.78539816339744830962;
     const double t = e * e;
     const double se = e + (e * t) * (-1.0 / 6.0 + t * (1.0 / 120.0));
     const double ce = 1.0 + t * (-1.0 / 2.0 + t * (1.0 / 24.0));
@@ -417,15 +455,13 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                 // Plain form: the reference's operation order; comparisons on the
                 // integer ALU (dgt0/dlt_nn/dclamp01 give the IEEE results).
                 const double kInf = __longlong_as_double(0x7FF0000000000000LL);
+                // one division per axis: (1 - o)/d moving up, o/(-d) moving down
                 double T[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    if (dgt0(d[a]))
-                        T[a] = (1.0 - o[a]) / d[a];
-                    else if (dlt0(d[a]))
-                        T[a] = o[a] / (-d[a]);
-                    else
-                        T[a] = kInf;
+                    const double num = dgt0(d[a]) ? 1.0 - o[a] : o[a];
+                    const double den = __longlong_as_double(dbits(d[a]) & 0x7FFFFFFFFFFFFFFFLL);  // |d|
+                    T[a] = (dgt0(d[a]) || dlt0(d[a])) ? num / den : kInf;
                 }
                 double tau = 0.0;
 #pragma unroll  // unrolled: each event index is a constant (measured 5 % faster, FP32)
@@ -468,7 +504,8 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                             for (int a = 0; a < 3; ++a) {
                                 d[a] = n[a] * sc;
                                 if (dbits(T[a]) == 0x7FF0000000000000LL) continue;
-                                T[a] = dgt0(d[a]) ? tau + (1.0 - o[a]) / d[a] : tau + o[a] / (-d[a]);
+                                const double num = dgt0(d[a]) ? 1.0 - o[a] : o[a];
+                                T[a] = tau + num / __longlong_as_double(dbits(d[a]) & 0x7FFFFFFFFFFFFFFFLL);
                             }
                         }
                     }
