@@ -424,6 +424,36 @@ def test_trajectory_independent_of_thread_split(oracle_lib):
         np.testing.assert_array_equal(r1[k][100:300], r3[k])
 
 
+def test_each_face_decision_is_an_independent_trial(oracle_lib):
+    """Every voxel its own label, one kappa for every pair and ds = 0.9
+    voxel, so a step meets up to three membranes (Sec. 2.2 items 3-4): with
+    equal D the number N of face events is set by the start and the
+    direction alone, and each event crosses with the same P, on its own
+    Bernoulli word.  Among walkers with N events the crossings are then
+    Binomial(N, P), with P = T/2^32 of the threshold table and T from Eq. 3
+    at P ~ 1/2 (a shared or reused word would put no mass on 0 < k < N)."""
+    lab = np.arange(64).reshape(4, 4, 4)
+    l_p, D = 0.1, 2.0
+    dt = (0.9 * l_p) ** 2 / (6 * D)
+    kappa = D / (ds_of(D, dt) * 2.0 / 3.0)        # kappa ds C3 / D = 1: P = 1/2 by Eq. 3
+    W = 400_000
+    wl = make_workload(lab, voxel_um=l_p, D=D, kappa=kappa, dt=dt, n_steps=1, n_walkers=W, seed=12)
+    T, _ = oracle_lib.thresholds(wl)
+    P = float(T[0, 1]) / 2.0 ** 32
+    assert abs(P - 0.5) < 1e-9 and np.all(T[~np.eye(64, dtype=bool)] == T[0, 1])
+    r = oracle_lib.run(wl, n_threads=NT, hash_=False)
+    ev, cross, refl = r["counts"][:, 0], r["counts"][:, 1], r["counts"][:, 2]
+    np.testing.assert_array_equal(ev, cross + refl)   # every face is a membrane
+    for N in (1, 2, 3):
+        m = ev == N
+        n = int(m.sum())
+        assert n > 2000, N
+        for k in range(N + 1):
+            expect = math.comb(N, k) * P ** k * (1 - P) ** (N - k)
+            f = float((cross[m] == k).mean())
+            assert abs(f - expect) < Z * math.sqrt(expect * (1 - expect) / n), (N, k, f, expect)
+
+
 def test_finite_step_permeability_correction(oracle_lib):
     """App. C, Eq. C.7: with the uncorrected P of Eq. 2 the walk realises
     kappa / (1 - alpha), alpha = (P12 + P21) / 2; Eq. 3 removes this to first
