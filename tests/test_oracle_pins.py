@@ -413,6 +413,27 @@ def test_uniform_initial_density(oracle_lib):
         assert np.all(np.abs(h - W / 10) < Z * math.sqrt(W / 10))
 
 
+def test_initial_position_uniform_jointly(oracle_lib):
+    """Sec. 2.2 item 1, jointly: the start point (voxel and offset together)
+    is uniform over the live volume, so each octant of each live voxel holds
+    1/(8 n_live) of the walkers.  Per-axis histograms cannot see a word
+    shared between two offsets, or between the voxel draw and an offset;
+    either empties whole octants here."""
+    lab = np.zeros((4, 4, 4), np.uint16)
+    lab[0] = 1
+    W = 192_000
+    wl = make_workload(lab, voxel_um=0.2, D=2.0, dt=1e-3, n_steps=0, n_walkers=W, dead=[0, 1], seed=5)
+    r = oracle_lib.run(wl, n_threads=NT)
+    v = np.mod(r["i0"][:, 0], 4) + 4 * (np.mod(r["i0"][:, 1], 4) + 4 * np.mod(r["i0"][:, 2], 4))
+    octant = (r["o0"] >= 0.5).astype(np.int64) @ np.array([1, 2, 4])
+    cnt = np.bincount(v * 8 + octant, minlength=64 * 8)[16 * 8:]
+    e = W / cnt.size
+    assert np.all(np.abs(cnt - e) < Z * math.sqrt(e)), (cnt.min(), cnt.max(), e)
+    chi2 = float(((cnt - e) ** 2 / e).sum())
+    dof = cnt.size - 1
+    assert abs(chi2 - dof) < Z * math.sqrt(2 * dof), chi2
+
+
 def test_trajectory_independent_of_thread_split(oracle_lib):
     wl = make_workload(np.arange(8).reshape(2, 2, 2) % 3, voxel_um=0.2, D=2.0, kappa=5.0, dt=1e-3,
                        n_steps=200, n_walkers=500, seed=99)
