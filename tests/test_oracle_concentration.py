@@ -95,6 +95,26 @@ def test_initial_density_follows_concentration(oracle_lib):
     assert abs(f - expect) < Z * math.sqrt(expect * (1 - expect) / W), (f, expect)
 
 
+def test_start_offsets_stay_uniform_with_concentrations(oracle_lib):
+    """The concentration-weighted start changes only how often each label is
+    chosen: inside the chosen voxel the offset stays uniform on every axis,
+    in the low-concentration label too (the acceptance uses a word of its
+    own, not one of the offset's)."""
+    lab = slabs(3, 5)
+    conc = np.array([1.0, 0.3])
+    W = 200000
+    wl = make_workload(lab, voxel_um=0.2, D=[2.0, 1.0], kappa=0.1, dt=1e-3, n_steps=0, n_walkers=W, seed=9,
+                       conc=conc)
+    r = oracle_lib.run(wl, n_threads=NT, hash_=False)
+    assert r["err"] == 0
+    for c in (0, 1):
+        m = r["c"] == c
+        for a in range(3):
+            h, _ = np.histogram(r["o0"][m, a], bins=10, range=(0, 1))
+            e = m.sum() / 10
+            assert np.all(np.abs(h - e) < Z * math.sqrt(e)), (c, a, h, e)
+
+
 @pytest.mark.parametrize("model", ["kappa-lambda0", "kappa-optimal", "baxter"])
 def test_threshold_ratio_keeps_equilibrium(oracle_lib, model):
     """P12 / P21 = c2 sqrt(D2) / (c1 sqrt(D1)) for every pair, which keeps

@@ -43,6 +43,33 @@ def test_walkers_never_leave_a_closed_voxel(oracle_lib, interaction):
         np.testing.assert_allclose(step, s, rtol=1e-12)
 
 
+def test_rejection_stays_are_counted_at_the_refusal_rate(oracle_lib):
+    """Rejection sampling in closed voxels: the start is uniform and stays
+    uniform (App. B), and a step from a uniform point of the unit voxel along
+    s n stays inside with probability prod_a (1 - s |n_a|), so the stays per
+    step (the third count) average 1 - E_n prod_a (1 - s |n_a|) over
+    directions (quadrature over the sphere).  No face event survives a
+    refusal, and nothing crosses."""
+    lab = np.arange(64).reshape(4, 4, 4)
+    dt, l_p, D, n = 1e-3, 0.2, 2.0, 40
+    s = ds_of(D, dt) / l_p
+    W = 20000
+    wl = make_workload(lab, voxel_um=l_p, D=D, kappa=0.0, dt=dt, n_steps=n, n_walkers=W, seed=13, interaction=RS)
+    r = oracle_lib.run(wl, n_threads=NT)
+    cnt = r["counts"]
+    assert np.all(cnt[:, 0] == 0) and np.all(cnt[:, 1] == 0)
+    # E over the sphere: z uniform on [-1, 1], azimuth uniform (midpoint rule)
+    m = 2000
+    z = -1 + (np.arange(m) + 0.5) * (2.0 / m)
+    ph = (np.arange(m) + 0.5) * (2 * math.pi / m)
+    rr = np.sqrt(1 - z * z)[:, None]
+    nx, ny, nz = np.abs(rr * np.cos(ph)), np.abs(rr * np.sin(ph)), np.abs(z)[:, None]
+    stay_in = ((1 - s * nx) * (1 - s * ny) * (1 - s * nz)).mean()
+    per = cnt[:, 2] / n
+    expect = 1 - stay_in
+    assert abs(per.mean() - expect) < Z * per.std() / math.sqrt(W), (per.mean(), expect)
+
+
 def _slab_positions(r, a_vox):
     """Distance (voxels) of each walker to the nearest wall of its slab."""
     x = np.mod(r["i"][:, 0], 2 * a_vox) + r["o"][:, 0]

@@ -82,6 +82,24 @@ def test_one_step_saturation_is_rho_s_over_v(oracle_lib, interaction):
         assert abs(expect - rho * (2 / a) * dt) < 1e-6 * expect + 2.0 ** -32
 
 
+def test_membrane_into_a_dead_label_absorbs(oracle_lib):
+    """Sec. 2.1.3 with the other side dead (e.g. myelin): walkers live only
+    between the planes, the dead label is never entered, and the membrane
+    still saturates: the first step's saturated fraction is again
+    ds/(2a) P_MT."""
+    a_vox, l_p, dt, rho, D = 6, 0.1, 5e-4, 15.0, 2.0
+    a = a_vox * l_p
+    W = 400_000
+    wl = make_workload(slabs(a_vox), voxel_um=l_p, D=D, dt=dt, n_steps=1, n_walkers=W, seed=8, rho=rho,
+                       dead=[0, 1])
+    r = oracle_lib.run(wl, n_threads=NT, hash_=False)
+    assert np.all(r["c"] == 0)
+    P = p_hat(rho, D, dt)
+    f = saturated(r).mean()
+    expect = ds_of(D, dt) / (2 * a) * P
+    assert abs(f - expect) < Z * math.sqrt(expect * (1 - expect) / W), (f, expect)
+
+
 def test_one_step_saturation_under_erl(oracle_lib):
     """ERL redraws after every refused draw, and each refused draw meets the
     plane once: from u = h/ds < 1 the number of refused draws N is geometric

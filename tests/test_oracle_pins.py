@@ -434,6 +434,76 @@ def test_initial_position_uniform_jointly(oracle_lib):
     assert abs(chi2 - dof) < Z * math.sqrt(2 * dof), chi2
 
 
+def test_start_voxels_on_a_non_cubic_grid(oracle_lib):
+    """Sec. 2.2 item 1 on a 3 x 5 x 4 grid (x, y, z) with an irregular dead
+    label: every walker starts in a live voxel with that voxel's label, and
+    the live voxels are equally likely (the raster order is x fastest, so a
+    decode that mixes up the axis sizes breaks both)."""
+    rng = np.random.default_rng(3)
+    lab = rng.integers(0, 3, size=(4, 5, 3))  # (nz, ny, nx)
+    dead = np.array([0, 0, 1], np.uint8)
+    W = 60_000
+    wl = make_workload(lab, voxel_um=0.2, D=2.0, dt=1e-3, n_steps=0, n_walkers=W, dead=dead, seed=6)
+    r = oracle_lib.run(wl, n_threads=NT)
+    x, y, z = r["i0"][:, 0], r["i0"][:, 1], r["i0"][:, 2]
+    assert x.min() >= 0 and x.max() < 3 and y.min() >= 0 and y.max() < 5 and z.min() >= 0 and z.max() < 4
+    np.testing.assert_array_equal(lab[z, y, x], r["c"])
+    live = dead[lab] == 0
+    cnt = np.bincount((z * 5 + y) * 3 + x, minlength=60).reshape(4, 5, 3)
+    assert np.all(cnt[~live] == 0)
+    e = W / live.sum()
+    assert np.all(np.abs(cnt[live] - e) < Z * math.sqrt(e)), (cnt[live].min(), cnt[live].max(), e)
+
+
+def test_readout_weights_are_the_relaxation_weights(oracle_lib):
+    """Eq. 5 and Eq. 7: S = sum alpha e^{-i phi} / sum alpha.  One label with
+    T2 = TE / 2: every walker has alpha = e^{-2}, so sum alpha = W e^{-2}, and
+    alpha cancels from S, which stays the exact free-walk signal
+    prod_j sinc(q H_j ds)."""
+    W, n, dt = 40000, 60, 1e-3
+    G = np.zeros(n)
+    G[:20] = 1.0
+    G[40:60] = -1.0
+    T2 = n * dt / 2.0
+    wl = make_workload(np.zeros((8, 8, 8)), voxel_um=0.2, D=2.0, T2=T2, dt=dt, n_steps=n, G=G,
+                       dirs=np.array([[1.0, 0, 0]]), b=np.array([0.0, 1.0]), n_walkers=W, seed=15)
+    r = oracle_lib.run(wl, n_threads=NT)
+    S, asum = oracle_lib.readout(r, wl)
+    assert abs(asum - W * math.exp(-2.0)) < 1e-12 * asum
+    assert abs(S[0, 0, 0] - 1.0) < 1e-12
+    bs = oracle_lib.bvalue(G, dt)
+    H = dt * np.cumsum(G[::-1])[::-1]
+    x = math.sqrt(1.0 / bs) * H * ds_of(2.0, dt)
+    expect = np.prod(np.where(x == 0, 1.0, np.sin(x) / np.where(x == 0, 1.0, x)))
+    phi = math.sqrt(1.0 / bs) * r["phase"][:, 0, 0]
+    assert abs(S[0, 0, 1].real - expect) < Z * np.cos(phi).std() / math.sqrt(W), (S[0, 0, 1], expect)
+
+
+def test_tied_face_times_go_to_the_lower_axis(oracle_lib):
+    """Two faces met at the same time (a diagonal step from a symmetric
+    point): the x face is the step's event 0 and takes the first Bernoulli
+    word, the y face event 1 and the second.  With the first word crossing
+    and the second reflecting, the walker ends one voxel along x, mirrored
+    in y (unfolded end point: x - 1, 2 - y)."""
+    lab = np.zeros((2, 2, 2), np.int64)
+    lab[:, 0, 1], lab[:, 1, 0], lab[:, 1, 1] = 1, 2, 3
+    wl = _lattice_wl(lab, 5.0, D=2.0, dt=1e-3, voxel=0.2)
+    T, svec = oracle_lib.thresholds(wl)
+    s = svec[0]
+    assert 0 < T[0, 1] < 2 ** 32 - 1 and T[1, 3] > 0
+    n0 = np.array([1.0, 1.0, 0.0]) / math.sqrt(2.0)
+    o0 = np.array([0.8, 0.8, 0.5])
+    assert (1 - 0.8) / (s * n0[0]) < 1.0
+    i, o, c, A, n, counts, err = oracle_lib.walk_once(wl, [0, 0, 0], o0, 0, n0.copy(), perm=[0, 2 ** 32 - 1, 0])
+    assert err == 0
+    np.testing.assert_array_equal(i, [1, 0, 0])
+    assert c == 1
+    p = o0 + s * n0
+    np.testing.assert_allclose(o, [p[0] - 1.0, 2.0 - p[1], 0.5], atol=1e-12)
+    np.testing.assert_array_equal(n, [n0[0], -n0[1], 0.0])
+    assert list(counts) == [2, 1, 1]
+
+
 def test_trajectory_independent_of_thread_split(oracle_lib):
     wl = make_workload(np.arange(8).reshape(2, 2, 2) % 3, voxel_um=0.2, D=2.0, kappa=5.0, dt=1e-3,
                        n_steps=200, n_walkers=500, seed=99)
