@@ -45,11 +45,26 @@ def test_free_walk_moments(oracle_lib, n):
         x2, x4 = dx[:, a] ** 2, dx[:, a] ** 4
         assert abs(x2.mean() - n * m2x) < Z * x2.std() / math.sqrt(W)
         assert abs(x4.mean() - m4x) < Z * x4.std() / math.sqrt(W)
-    # the moment sums the oracle accumulates match the final positions
+    # every one of the 22 moment sums against the isotropic-step expectation:
+    # a product with an odd power of some axis averages 0; x_a^2 x_b^2 (a != b)
+    # averages n ds^4/15 + n (n-1) (ds^2/3)^2 (one step: <u_a^2 u_b^2> = 1/15)
     M = r["moments"][-1]
     np.testing.assert_allclose(M[0], W, rtol=1e-14)
-    np.testing.assert_allclose(M[1], (dx[:, 0] ** 2).sum(), rtol=1e-12)
-    np.testing.assert_allclose(M[21], (dx[:, 2] ** 4).sum(), rtol=1e-12)
+    m22 = n * ds ** 4 / 15 + n * (n - 1) * m2x ** 2
+    for q, name in enumerate(oracle_lib.MOMENT_NAMES[1:], start=1):
+        powers = [name.count(ax) for ax in "xyz"]
+        prod = np.prod([dx[:, a] ** powers[a] for a in range(3)], axis=0)
+        if any(p % 2 for p in powers):
+            expect = 0.0
+        elif len(name) == 2:
+            expect = n * m2x
+        elif 4 in powers:
+            expect = m4x
+        else:
+            expect = m22
+        assert abs(M[q] / W - expect) < Z * prod.std() / math.sqrt(W), (name, M[q] / W, expect)
+        # and the sum the oracle accumulated is that of its exported final positions
+        assert abs(M[q] - prod.sum()) <= 1e-12 * np.abs(prod).sum(), name
 
 
 def test_face_events_per_step(oracle_lib):
