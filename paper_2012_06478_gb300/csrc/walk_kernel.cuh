@@ -122,7 +122,7 @@ __device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, const d
 {
     // z = 1 - 2 u(x0) = k 2^-32 with the odd integer k = 2^32 - 1 - 2 x0, and
     // (1 - z)(1 + z) = (2^64 - k^2) 2^-64 rounded once: both from integers,
-    // the same bits as the reference's step-by-step evaluation.
+    // the same bits as the CPU FP64 reference's step-by-step evaluation.
     const bool zneg = x0 >= 0x80000000u;
     const uint32_t kmag = zneg ? 2u * x0 + 1u : 0xFFFFFFFFu - 2u * x0;  // |k|
     const double z = odd_scaled(kmag, zneg, -32);
@@ -452,7 +452,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
             // reflector), and a crossing into a label of another step length
             // recomputes the remaining times from the current positions.
             if constexpr (kF64) {
-                // Plain form: the reference's operation order; comparisons on the
+                // Plain form: the CPU FP64 reference's operation order; comparisons on the
                 // integer ALU (dgt0/dlt_nn/dclamp01 give the IEEE results).
                 const double kInf = __longlong_as_double(0x7FF0000000000000LL);
                 // one division per axis: (1 - o)/d moving up, o/(-d) moving down
