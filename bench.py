@@ -117,12 +117,16 @@ def workload_of(name, interaction="ec", rho=0.0):
 
 
 def events_per_step(wl):
-    """Expected face events per walker-step, 1.5 ds / l_p (walker-averaged
-    over labels by volume fraction; exact for any lattice)."""
+    """Expected face events per walker-step, 1.5 ds / l_p (exact for any
+    lattice), averaged over labels by where the walkers are: the live
+    volume, weighted by the spin concentration when there is one."""
     lab = wl.labels
-    frac = np.bincount(lab.ravel(), minlength=wl.n_labels) / lab.size
+    w = np.bincount(lab.ravel(), minlength=wl.n_labels).astype(np.float64)
+    w *= np.asarray(wl.dead) == 0
+    if wl.conc is not None:
+        w *= np.asarray(wl.conc, np.float64)
     ds = np.sqrt(6.0 * wl.D * wl.dt)
-    return float((frac * 1.5 * ds / wl.voxel_um).sum())
+    return float((w / w.sum() * 1.5 * ds / wl.voxel_um).sum())
 
 
 def cpu_baseline(wl, seconds=12.0, threads=0):
@@ -463,11 +467,10 @@ def serving(rms, ri, capacity, n_requests, precision, sp):
                       "walkers 1e4-1e6 and steps 1e3-5e4 log-uniform, 6-64 directions"}
 
 
-def paired_sigma(torch, wl, b_s, w64, w32):
+def paired_sigma(torch, wl, b_s, w64, w32, dev="cuda"):
     """Per (shape, dir, b): the standard error of the mean of the paired
     per-walker differences alpha e^{-i phi} / <alpha> (FP32 form minus FP64
-    form, same walkers).  Computed on the GPU in walker chunks."""
-    dev = "cuda"
+    form, same walkers).  Computed on the device in walker chunks."""
     f64 = torch.float64
     q = torch.tensor(np.sqrt(np.asarray(wl.b)[None, :] / np.asarray(b_s)[:, None]), dtype=f64, device=dev)
     dirs = torch.tensor(np.asarray(wl.dirs), dtype=f64, device=dev)
