@@ -42,3 +42,40 @@ def test_serving_requests_seeded():
     r1 = ri.serving_requests(20, 4)
     assert r1 == ri.serving_requests(20, 4)
     assert all(1e4 <= r["n_walkers"] <= 1e6 and 6 <= r["n_dirs"] <= 64 for r in r1)
+
+
+def test_axon_generator_follows_the_recipe():
+    """The 200-axon recipe on a shorter stack (20 x 20 x 8 um, 0.1 um voxels):
+    every axon is present, the narrowest cross-section of each axon (away
+    from its beads) gives back the base radius distribution Gamma(6.25, 0.08)
+    clipped at 0.15 um (mean 0.5, sd 0.2), about half the volume is
+    intra-axonal, and the volume continues across the periodic z boundary."""
+    import math
+    nz = 80
+    lab = ri.axon_labels(200, 200, nz, 0.1, 200, seed=2)
+    present = np.unique(lab)
+    assert present[0] == 0 and list(present[1:]) == list(range(1, 201))
+    area = np.stack([np.bincount(lab[z].ravel(), minlength=201) for z in range(nz)])  # (z, label)
+    r_min = np.sqrt(area[:, 1:].min(axis=0) / math.pi) * 0.1
+    assert abs(r_min.mean() - 0.5) < 4.5 * 0.2 / math.sqrt(200), r_min.mean()
+    assert 0.15 < r_min.std() < 0.25, r_min.std()
+    assert r_min.min() >= 0.15 - 0.1
+    assert 0.4 < (lab > 0).mean() < 0.7
+    step = [(lab[z] != lab[z + 1]).mean() for z in range(nz - 1)]
+    assert (lab[nz - 1] != lab[0]).mean() <= 3 * max(step)
+
+
+def test_voronoi_generator_is_the_periodic_nearest_seed_map():
+    """Every voxel centre takes its nearest seed under the periodic (minimum
+    image) distance: checked by brute force over all seeds on a 16^3 grid."""
+    n, cells, seed = 16, 20, 7
+    lab = ri.voronoi_labels(n, cells, seed)
+    seeds = np.random.default_rng(seed).uniform(0, n, size=(cells, 3))   # the generator's seed draw
+    g = np.arange(n) + 0.5
+    z, y, x = np.meshgrid(g, g, g, indexing="ij")
+    p = np.stack([x, y, z], axis=-1)[..., None, :]                        # (n, n, n, 1, 3)
+    d = np.abs(p - seeds)
+    d = np.minimum(d, n - d)
+    expect = np.argmin((d * d).sum(axis=-1), axis=-1)
+    np.testing.assert_array_equal(lab, expect)
+    assert len(np.unique(lab)) == cells
