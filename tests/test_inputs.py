@@ -79,3 +79,20 @@ def test_voronoi_generator_is_the_periodic_nearest_seed_map():
     expect = np.argmin((d * d).sum(axis=-1), axis=-1)
     np.testing.assert_array_equal(lab, expect)
     assert len(np.unique(lab)) == cells
+
+
+def test_ogse_waveform_b_value():
+    """Cosine OGSE, n periods per lobe at frequency f: q(t) = sin(2 pi f t)/(2 pi f)
+    over each lobe, so b = 2 int_0^T q^2 dt = n / (4 pi^2 f^3) (ms/um^2 for f in
+    1/ms); the step-averaged waveform's discrete b_s tends to it as dt -> 0."""
+    import math
+    import oracle
+    oracle.build()
+    for f_hz, n_per in ((100.0, 1), (40.0, 2)):
+        f = f_hz * 1e-3
+        dt = 4e-4
+        n = int(math.ceil(2 * n_per / f / dt)) + 10
+        G = ri.ogse(f_hz, dt, n, n_periods=n_per)
+        exact = n_per / (4 * math.pi ** 2 * f ** 3)
+        assert abs(oracle.bvalue(G, dt) - exact) < 1e-3 * exact, (f_hz, oracle.bvalue(G, dt), exact)
+        assert abs(G.sum()) < 1e-9 and np.all(G[int(2 * n_per / f / dt) + 2:] == 0.0)
