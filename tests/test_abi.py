@@ -47,3 +47,33 @@ def test_invalid_arguments_rejected_on_host():
     assert _lib.lib.rms_create_substrate(C.byref(d), C.byref(h)) == _lib.RMS_E_INVALID_ARG
     assert "null" in _lib.last_error()
     assert _lib.lib.rms_run(None, None, C.byref(h)) == _lib.RMS_E_INVALID_ARG
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """Every descriptor the binding passes by pointer has, field by field, the
+    offsets and size that a C compiler gives the struct in include/rms.h
+    (gcc on this host; the header includes only stddef.h and stdint.h)."""
+    import subprocess
+    from paper_2012_06478_gb300 import _lib
+    structs = {"rms_substrate_desc": _lib.SubstrateDesc, "rms_sequence_desc": _lib.SequenceDesc,
+               "rms_run_desc": _lib.RunDesc, "rms_run_state": _lib.RunState,
+               "rms_server_config": _lib.ServerConfig}
+    c_name = {"lam": "lambda"}  # the C member `lambda` is a Python keyword
+    lines = ['#include <stdio.h>', '#include "rms.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {c_name.get(fname, fname)}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    c_layout = {}
+    for ln in subprocess.check_output([str(exe)], text=True).splitlines():
+        cname, field, val = ln.split()
+        c_layout[(cname, field)] = int(val)
+    for cname, py in structs.items():
+        assert C.sizeof(py) == c_layout[(cname, "size")], cname
+        for fname, _ in py._fields_:
+            assert getattr(py, fname).offset == c_layout[(cname, fname)], (cname, fname)
