@@ -77,3 +77,25 @@ def test_ctypes_structs_match_the_header_layout(tmp_path):
         assert C.sizeof(py) == c_layout[(cname, "size")], cname
         for fname, _ in py._fields_:
             assert getattr(py, fname).offset == c_layout[(cname, fname)], (cname, fname)
+
+
+def test_binding_argument_counts_match_the_prototypes():
+    """Each ctypes signature takes as many arguments as its prototype in
+    include/rms.h, and returns a pointer-sized value exactly where the
+    prototype returns a pointer."""
+    from paper_2012_06478_gb300 import _lib
+    text = ""
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text += open(os.path.join(ROOT, "include", fn)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    protos = {}
+    for m in re.finditer(r"^\s*((?:const\s+)?[a-z_0-9]+\s*\**)\s*(rms_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", text, re.M | re.S):
+        ret, name, params = m.group(1), m.group(2), " ".join(m.group(3).split())
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        protos[name] = (n, "*" in ret)
+    assert set(protos) == set(_lib.SIGNATURES)
+    for name, (args, res) in _lib.SIGNATURES.items():
+        n, ptr = protos[name]
+        assert len(args) == n, (name, len(args), n)
+        assert ptr == (res in (C.c_char_p, C.c_void_p)), name
