@@ -99,3 +99,21 @@ def test_binding_argument_counts_match_the_prototypes():
         n, ptr = protos[name]
         assert len(args) == n, (name, len(args), n)
         assert ptr == (res in (C.c_char_p, C.c_void_p)), name
+
+
+def test_package_refuses_to_import_without_the_library(tmp_path):
+    """No CPU fallback: a copy of the package without librms.so fails to
+    import, naming the missing library."""
+    import shutil
+    import subprocess
+    import sys
+    src = os.path.join(ROOT, "paper_2012_06478_gb300")
+    dst = tmp_path / "paper_2012_06478_gb300"
+    dst.mkdir()
+    for fn in os.listdir(src):
+        if fn.endswith(".py"):
+            shutil.copy(os.path.join(src, fn), dst / fn)
+    r = subprocess.run([sys.executable, "-c", "import paper_2012_06478_gb300"], cwd=tmp_path,
+                       capture_output=True, text=True, env={**os.environ, "PYTHONPATH": str(tmp_path)})
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "librms.so" in r.stderr and "no CPU fallback" in r.stderr
