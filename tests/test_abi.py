@@ -117,3 +117,15 @@ def test_package_refuses_to_import_without_the_library(tmp_path):
                        capture_output=True, text=True, env={**os.environ, "PYTHONPATH": str(tmp_path)})
     assert r.returncode != 0
     assert "ImportError" in r.stderr and "librms.so" in r.stderr and "no CPU fallback" in r.stderr
+
+
+def test_product_code_never_reaches_the_oracle():
+    """The oracle is test infrastructure: neither the package nor the input
+    generators import it, and the package links nothing from oracle/."""
+    pat = re.compile(r"^\s*(import\s+oracle\b|from\s+oracle\b)|librms_oracle|rms_oracle\.c", re.M)
+    for top in ("paper_2012_06478_gb300", "rms_inputs"):
+        for dirpath, _, files in os.walk(os.path.join(ROOT, top)):
+            for fn in files:
+                if fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                    text = open(os.path.join(dirpath, fn), encoding="utf-8").read()
+                    assert not pat.search(text), os.path.join(dirpath, fn)
