@@ -70,6 +70,31 @@ def test_rejection_stays_are_counted_at_the_refusal_rate(oracle_lib):
     assert abs(per.mean() - expect) < Z * per.std() / math.sqrt(W), (per.mean(), expect)
 
 
+def test_erl_leap_limit_near_the_centre_of_a_closed_voxel(oracle_lib):
+    """App. A's redraw loop is capped at 64 draws (R21).  With ds = 0.95 voxel
+    in closed voxels, a start within r < 0.95 - sqrt(3)/2 of the voxel's
+    centre reaches at most sqrt(3)/2 + r: every direction leaves the voxel,
+    so the walker stays for the step (one stay in the counts) and the run
+    reports the leap-limit error bit (16).  Walkers elsewhere still move ds."""
+    lab = np.arange(64).reshape(4, 4, 4)
+    l_p, D = 0.1, 2.0
+    dt = (0.95 * l_p) ** 2 / (6 * D)
+    W = 40000
+    wl = make_workload(lab, voxel_um=l_p, D=D, kappa=0.0, dt=dt, n_steps=1, n_walkers=W, seed=14,
+                       interaction=ERL)
+    r = oracle_lib.run(wl, n_threads=NT)
+    assert r["err"] & 16
+    rc = np.linalg.norm(r["o0"] - 0.5, axis=1)
+    trapped = rc < 0.95 - math.sqrt(3) / 2 - 1e-9
+    assert trapped.sum() > 50
+    np.testing.assert_array_equal(r["o"][trapped], r["o0"][trapped])
+    np.testing.assert_array_equal(r["counts"][trapped, 2], 1)
+    moved = np.linalg.norm(r["o"] - r["o0"], axis=1)
+    free = rc > 0.2
+    np.testing.assert_allclose(moved[free & (moved > 0)], 0.95, rtol=1e-12)
+    assert (moved[free] > 0).mean() > 0.9
+
+
 def _slab_positions(r, a_vox):
     """Distance (voxels) of each walker to the nearest wall of its slab."""
     x = np.mod(r["i"][:, 0], 2 * a_vox) + r["o"][:, 0]
