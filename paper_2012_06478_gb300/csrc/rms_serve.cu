@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -87,13 +88,16 @@ struct rms_server {
     BlockTask *h_tasks[2] = {nullptr, nullptr}, *d_tasks[2] = {nullptr, nullptr};
     int64_t task_cap = 0;
     cudaEvent_t buf_ev[2] = {nullptr, nullptr};
-    int64_t tick = 0;
+    // written by the scheduler thread only; atomic because rms_server_stats
+    // reads them from other threads while it runs
+    std::atomic<int64_t> tick{0};
     cudaGraphExec_t exec = nullptr;
-    int64_t graph_updates = 0, graph_instantiations = 0;
+    std::atomic<int64_t> graph_updates{0}, graph_instantiations{0};
     std::vector<std::pair<double *, size_t>> pinned_pool;
     // statistics
     std::vector<double> lat_ms;
-    double walker_steps = 0;
+    std::atomic<double> walker_steps{0.0};  // scheduler thread only (see tick)
+    std::atomic<int> in_flight{0};          // active + finalizing, published by the scheduler thread
     Clock::time_point t_first, t_last;
     bool have_first = false;
     int64_t completed = 0;
@@ -101,6 +105,13 @@ struct rms_server {
 };
 
 namespace {
+
+// active + finalizing for rms_server_stats; called by the scheduler thread,
+// the only writer of both lists, after it changes either
+void publish_in_flight(rms_server *s)
+{
+    s->in_flight.store((int)(s->active.size() + s->finalizing.size()));
+}
 
 double *take_pinned(rms_server *s, size_t bytes)
 {
@@ -130,9 +141,12 @@ rms_status grow_tasks(rms_server *s, int64_t need)
     return RMS_OK;
 }
 
+// The sequence reference is released under the same lock that makes the
+// failure visible: a waiter may delete the request as soon as it sees it.
 void fail_request(rms_server *s, Request *q, rms_status err, const char *msg)
 {
     std::lock_guard<std::mutex> lk(s->mu);
+    q->seq->refs.fetch_sub(1);
     q->st = St::Failed;
     q->err = err;
     q->msg = msg;
@@ -165,7 +179,6 @@ void admit(rms_server *s)
         rms_run_handle *r = new (std::nothrow) rms_run_handle();
         if (!r) {
             fail_request(s, q, RMS_E_OOM, "host allocation");
-            q->seq->refs.fetch_sub(1);
             continue;
         }
         r->seq = q->seq;
@@ -184,8 +197,11 @@ void admit(rms_server *s)
         if (st != RMS_OK) {
             run_free(r, true);
             delete r;
+            if (q->h_out) {  // back to the pool: the request never ran
+                s->pinned_pool.emplace_back(q->h_out, q->h_out_bytes);
+                q->h_out = nullptr;
+            }
             fail_request(s, q, st, rms_last_error());
-            q->seq->refs.fetch_sub(1);
             continue;
         }
         int slot;
@@ -209,6 +225,7 @@ void admit(rms_server *s)
         q->bucket = bucket_of(q->seq->S);
         s->mem_used += need;
         s->active.push_back(q);
+        publish_in_flight(s);
         std::lock_guard<std::mutex> lk(s->mu);
         q->st = St::Active;
         s->peak_active = std::max<int>(s->peak_active, (int)(s->active.size() + s->finalizing.size()));
@@ -219,7 +236,7 @@ void admit(rms_server *s)
 rms_status tick_once(rms_server *s)
 {
     NvtxRange nvtx_range("rms: serving tick");
-    const int j = (int)(s->tick & 1);
+    const int j = (int)(s->tick.load() & 1);
     RMS_CUDA(cudaEventSynchronize(s->buf_ev[j]));  // the upload from buffer j has run
     // drop cancelled requests from the active set (their memory is released
     // stream-ordered, after every launch that may still use it)
@@ -243,6 +260,7 @@ rms_status tick_once(rms_server *s)
             q->seq->refs.fetch_sub(1);
             s->cv_done.notify_all();
             s->active.erase(s->active.begin() + i);
+            publish_in_flight(s);
         } else {
             ++i;
         }
@@ -304,7 +322,7 @@ rms_status tick_once(rms_server *s)
     // requests that have taken all their steps: reductions, read-out, copy-back
     for (size_t i = 0; i < s->active.size();) {
         Request *q = s->active[i];
-        s->walker_steps += (double)q->W * (double)(range[i].second - range[i].first);
+        s->walker_steps.store(s->walker_steps.load() + (double)q->W * (double)(range[i].second - range[i].first));
         q->progress = range[i].second;
         if (q->progress >= q->seq->n_steps) {
             rms_run_handle *r = q->run;
@@ -323,6 +341,7 @@ rms_status tick_once(rms_server *s)
             }
             s->finalizing.push_back(q);
             s->active.erase(s->active.begin() + i);
+            publish_in_flight(s);
             range.erase(range.begin() + i);
         } else {
             ++i;
@@ -373,6 +392,7 @@ void poll_finalizing(rms_server *s)
         q->seq->refs.fetch_sub(1);
         s->cv_done.notify_all();
         s->finalizing.erase(s->finalizing.begin() + i);
+        publish_in_flight(s);
     }
 }
 
@@ -418,6 +438,7 @@ void scheduler(rms_server *s)
                 }
                 s->active.clear();
                 s->finalizing.clear();
+                publish_in_flight(s);
                 s->cv_done.notify_all();
             }
         }
@@ -581,14 +602,14 @@ extern "C" rms_status rms_server_stats(rms_server *s, double *out)
     out[0] = pct(0.50);
     out[1] = pct(0.99);
     out[2] = mean;
-    out[3] = span > 0 ? s->walker_steps / span : 0.0;
+    out[3] = span > 0 ? s->walker_steps.load() / span : 0.0;
     out[4] = (double)s->completed;
-    out[5] = (double)(s->active.size() + s->finalizing.size());
+    out[5] = (double)s->in_flight.load();
     out[6] = (double)s->pending.size();
     out[7] = (double)s->peak_active;
-    out[8] = (double)s->tick;
-    out[9] = (double)s->graph_updates;
-    out[10] = (double)s->graph_instantiations;
+    out[8] = (double)s->tick.load();
+    out[9] = (double)s->graph_updates.load();
+    out[10] = (double)s->graph_instantiations.load();
     return RMS_OK;
 }
 
