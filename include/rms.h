@@ -271,6 +271,25 @@ rms_status rms_cancel(rms_run_handle *run);
 rms_status rms_read_signal(rms_run_handle *run, double *S_re, double *S_im, double *moments,
                            double *alpha_sum);
 
+/* Wait for the run and copy its UNNORMALISED reductions to host memory, for
+ * combining runs over disjoint walker ranges of one simulation (walker
+ * shards on several ranks, Sec. 2.1.5 runs walkers independently): sums over
+ * walkers before the division by sum alpha of Eq. 7.  Any pointer may be
+ * NULL; layouts as rms_read_signal:
+ *   num_re, num_im : n_shapes*n_dirs*n_b, sum over walkers of alpha e^{-i phi}
+ *   alpha_sum      : 1 double, sum over walkers of alpha at the end
+ *   moments        : n_rec*22 sums (as rms_read_signal)
+ * Shards combine by adding these element by element; rms_normalise_partials
+ * then gives S.  Return codes as rms_read_signal. */
+rms_status rms_read_partials(rms_run_handle *run, double *num_re, double *num_im, double *alpha_sum,
+                             double *moments);
+
+/* S = num / alpha_sum element by element (Eq. 7's normalisation), on host
+ * arrays of n_combo doubles; the division rms_read_signal applies.
+ * RMS_E_INVALID_ARG for n_combo < 0 or a null array. */
+rms_status rms_normalise_partials(int64_t n_combo, const double *num_re, const double *num_im, double alpha_sum,
+                                  double *S_re, double *S_im);
+
 /* Wait for the run and copy the final per-walker state to host memory (any
  * pointer may be NULL; return codes as rms_read_signal; a saturated walker's
  * A is +INFINITY): i (W*3 int32 unwrapped voxel index), o (W*3 double
@@ -303,11 +322,21 @@ rms_status rms_run_step_time_ms(rms_run_handle *run, float *ms);
 /* ------------------------------------------------------------------ */
 typedef struct rms_server rms_server;
 
+/* Tick policies of rms_server_config.policy */
+#define RMS_SERVE_STEPS 0 /* every active request advances steps_per_tick steps per tick (processor sharing by
+                             steps: a request's latency grows with its step count, whatever its size) */
+#define RMS_SERVE_FILL 1  /* size-aware: the batched launch of a precision takes as long as its largest
+                             requests need for steps_per_tick steps (their blocks span several waves of the
+                             GPU's block slots); a request whose blocks fit in one wave advances that many
+                             waves' worth of steps instead (up to 64 x steps_per_tick), so small requests run
+                             for the whole tick rather than waiting on the large ones */
+
 typedef struct {
     int64_t memory_budget_bytes; /* device memory for the walker state of admitted requests (0: 8 GiB);
                                     a request is admitted when it fits (or when nothing else runs) */
     int32_t max_active;          /* requests admitted at once, 1..1024 (0: 64) */
     int32_t steps_per_tick;      /* steps every active request advances per tick (0: 256) */
+    int32_t policy;              /* RMS_SERVE_STEPS (0) or RMS_SERVE_FILL */
 } rms_server_config;
 
 /* Start the scheduler thread on the current device. */
@@ -332,6 +361,13 @@ rms_status rms_server_poll(rms_server *srv, int64_t ticket);
 rms_status rms_server_wait(rms_server *srv, int64_t ticket, int64_t timeout_ms, double *S_re, double *S_im,
                            double *moments, double *alpha_sum);
 
+/* Timing of a finished request, before rms_server_wait releases its ticket:
+ * out[0] queueing (ms, submit to admission), out[1] latency (ms, submit to
+ * result), out[2] its walker-steps (walkers x steps), out[3] the ticks it
+ * took part in.  RMS_E_NOT_READY while it runs, RMS_E_INVALID_ARG for an
+ * unknown ticket or a null pointer. */
+rms_status rms_server_request_info(rms_server *srv, int64_t ticket, double *out);
+
 /* Withdraw a queued or running request (a finishing one still completes). */
 rms_status rms_server_cancel(rms_server *srv, int64_t ticket);
 
@@ -343,6 +379,19 @@ rms_status rms_server_stats(rms_server *srv, double *out);
 
 /* Cancel what is queued or running, stop the thread, free everything. */
 rms_status rms_server_destroy(rms_server *srv);
+
+/* ------------------------------------------------------------------ */
+/* The counter-based generator behind every random draw (Sec. 2.2:     */
+/* directions, Bernoulli trials of Eq. 3, start points), exposed so    */
+/* that its words can be checked against other implementations.       */
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon et al., SC'11) on n (counter, key) pairs: DEVICE
+ * pointers ctr (n*4 uint32 words c0..c3), key (n*2 words k0, k1) and out (n*4
+ * words), the same function the walk kernels call with counter (walker_lo,
+ * walker_hi, step, tag << 16 | call) and key (seed_lo, seed_hi).  Enqueued on
+ * `stream` (cudaStream_t); returns without waiting.  RMS_E_INVALID_ARG for
+ * n < 0 or a null pointer with n > 0, RMS_E_CUDA. */
+rms_status rms_philox4x32_10(const uint32_t *ctr, const uint32_t *key, int64_t n, uint32_t *out, void *stream);
 
 /* ------------------------------------------------------------------ */
 /* Signal read-out that allocates nothing.  The paper has no           */

@@ -33,6 +33,13 @@ RMS_ERL = 2
 RMS_MAX_LEAPS = 64
 RMS_PERM_KAPPA = 0
 RMS_PERM_BAXTER = 1
+RMS_SERVE_STEPS = 0
+RMS_SERVE_FILL = 1
+RMS_PEAK_FP64_ADD = 0
+RMS_PEAK_FP64_MUL = 1
+RMS_PEAK_FP64_FMA = 2
+RMS_PEAK_GATHER = 3
+RMS_PEAK_GATHER_DEP = 4
 
 
 class RmsError(RuntimeError):
@@ -57,7 +64,8 @@ class SequenceDesc(C.Structure):
 
 
 class ServerConfig(C.Structure):
-    _fields_ = [("memory_budget_bytes", C.c_int64), ("max_active", C.c_int32), ("steps_per_tick", C.c_int32)]
+    _fields_ = [("memory_budget_bytes", C.c_int64), ("max_active", C.c_int32), ("steps_per_tick", C.c_int32),
+                ("policy", C.c_int32)]
 
 
 class RunDesc(C.Structure):
@@ -89,6 +97,9 @@ SIGNATURES = {
     "rms_cancel": ([C.c_void_p], C.c_int),
     "rms_read_signal": ([C.c_void_p] + [C.c_void_p] * 4, C.c_int),
     "rms_read_walkers": ([C.c_void_p] + [C.c_void_p] * 8, C.c_int),
+    "rms_read_partials": ([C.c_void_p] + [C.c_void_p] * 4, C.c_int),
+    "rms_normalise_partials": ([C.c_int64, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p], C.c_int),
+    "rms_philox4x32_10": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "rms_destroy_run": ([C.c_void_p], C.c_int),
     "rms_run_step_time_ms": ([C.c_void_p, C.POINTER(C.c_float)], C.c_int),
     "rms_server_create": ([C.POINTER(ServerConfig), C.POINTER(C.c_void_p)], C.c_int),
@@ -97,10 +108,15 @@ SIGNATURES = {
     "rms_server_poll": ([C.c_void_p, C.c_int64], C.c_int),
     "rms_server_wait": ([C.c_void_p, C.c_int64, C.c_int64] + [C.c_void_p] * 4, C.c_int),
     "rms_server_cancel": ([C.c_void_p, C.c_int64], C.c_int),
+    "rms_server_request_info": ([C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "rms_server_stats": ([C.c_void_p, C.c_void_p], C.c_int),
     "rms_server_destroy": ([C.c_void_p], C.c_int),
     "rms_readout_noalloc": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
                              C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    # include/rms_peaks.h
+    "rms_measure_peak": ([C.c_int32, C.c_int64, C.c_double, C.c_int32, C.c_void_p, C.POINTER(C.c_double),
+                          C.POINTER(C.c_double)], C.c_int),
+    "rms_device_sm_count": ([C.POINTER(C.c_int32)], C.c_int),
 }
 
 

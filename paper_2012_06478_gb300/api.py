@@ -17,13 +17,17 @@ from typing import Optional, Sequence as Seq
 import numpy as np
 
 from . import _lib as L
-from ._lib import RMS_CHECKED, RMS_COUNTS, RMS_EC, RMS_ERL, RMS_FP32, RMS_FP64, RMS_RS, RMS_TRAJ_HASH, RmsError, check
+from ._lib import (RMS_CHECKED, RMS_COUNTS, RMS_EC, RMS_ERL, RMS_FP32, RMS_FP64, RMS_PEAK_FP64_ADD, RMS_PEAK_FP64_FMA,
+                   RMS_PEAK_FP64_MUL, RMS_PEAK_GATHER, RMS_PEAK_GATHER_DEP, RMS_RS, RMS_SERVE_FILL, RMS_SERVE_STEPS,
+                   RMS_TRAJ_HASH, RmsError, check)
 
 __all__ = ["rms_create_substrate", "rms_set_sequence", "rms_run", "rms_read_signal", "rms_read_walkers",
            "rms_read_counts", "rms_cancel", "rms_run_query", "rms_destroy_run", "rms_destroy_sequence",
            "rms_destroy_substrate", "rms_sequence_bvalues", "rms_run_step_time_ms", "simulate", "current_stream",
            "RMS_FP32", "RMS_FP64", "RMS_TRAJ_HASH", "RMS_CHECKED", "RMS_COUNTS", "RMS_EC", "RMS_RS", "RMS_ERL",
-           "RmsError", "MOMENT_NAMES", "Server"]
+           "RmsError", "MOMENT_NAMES", "Server", "rms_measure_peak", "rms_device_sm_count", "rms_read_partials",
+           "rms_normalise_partials", "rms_philox4x32_10", "RMS_PEAK_FP64_ADD", "RMS_PEAK_FP64_MUL", "RMS_PEAK_FP64_FMA",
+           "RMS_PEAK_GATHER", "RMS_PEAK_GATHER_DEP", "RMS_SERVE_STEPS", "RMS_SERVE_FILL"]
 
 MOMENT_NAMES = ["1", "xx", "xy", "xz", "yy", "yz", "zz", "xxxx", "xxxy", "xxxz", "xxyy", "xxyz", "xxzz", "xyyy",
                 "xyyz", "xyzz", "xzzz", "yyyy", "yyyz", "yyzz", "yzzz", "zzzz"]
@@ -244,6 +248,44 @@ def rms_read_signal(run: Run):
     return (re + 1j * im).reshape(q.n_shapes, q.n_dirs, q.n_b), mom, float(asum[0])
 
 
+def rms_read_partials(run: Run):
+    """Unnormalised reductions for combining walker shards: (sum of alpha
+    e^{-i phi} complex (n_shapes, n_dirs, n_b), moments (n_rec, 22), sum alpha)."""
+    q = run.seq
+    n = q.n_shapes * q.n_dirs * q.n_b
+    re, im = np.zeros(n), np.zeros(n)
+    mom = np.zeros((q.n_rec, 22))
+    asum = np.zeros(1)
+    run.status = check(L.lib.rms_read_partials(run.handle, re.ctypes.data, im.ctypes.data, asum.ctypes.data,
+                                               mom.ctypes.data if q.n_rec else None),
+                       allow=(L.RMS_OK, L.RMS_W_LEAP_LIMIT))
+    return (re + 1j * im).reshape(q.n_shapes, q.n_dirs, q.n_b), mom, float(asum[0])
+
+
+def rms_normalise_partials(num, alpha_sum: float) -> np.ndarray:
+    """S = num / sum alpha (Eq. 7), computed by the library."""
+    num = np.asarray(num, np.complex128)
+    re = np.ascontiguousarray(num.real.ravel())
+    im = np.ascontiguousarray(num.imag.ravel())
+    sr, si = np.zeros(re.size), np.zeros(re.size)
+    check(L.lib.rms_normalise_partials(re.size, re.ctypes.data, im.ctypes.data, float(alpha_sum), sr.ctypes.data,
+                                       si.ctypes.data))
+    return (sr + 1j * si).reshape(num.shape)
+
+
+def rms_philox4x32_10(ctr, key, stream: Optional[int] = None):
+    """The library's Philox4x32-10 on CUDA tensors ctr (n, 4) and key (n, 2)
+    of dtype int32/uint32; returns an (n, 4) tensor of words (same dtype)."""
+    import torch
+    assert ctr.is_cuda and key.is_cuda and ctr.is_contiguous() and key.is_contiguous()
+    n = ctr.shape[0]
+    assert ctr.shape == (n, 4) and key.shape == (n, 2) and ctr.element_size() == 4 and key.element_size() == 4
+    out = torch.empty_like(ctr)
+    check(L.lib.rms_philox4x32_10(ctr.data_ptr(), key.data_ptr(), n, out.data_ptr(),
+                                  current_stream() if stream is None else stream))
+    return out
+
+
 def rms_read_walkers(run: Run) -> dict:
     W, S = run.n_walkers, run.seq.n_shapes
     out = dict(i=np.zeros((W, 3), np.int32), o=np.zeros((W, 3)), i0=np.zeros((W, 3), np.int32),
@@ -306,7 +348,8 @@ def simulate(wl, precision: int = RMS_FP64, n_walkers: Optional[int] = None, see
                   int(getattr(wl, "interaction", RMS_EC)) if interaction is None else int(interaction),
                   resume=resume, step_end=step_end)
     S, mom, asum = rms_read_signal(run)
-    res = dict(S=S, moments=mom, alpha_sum=asum, status=seq.status, step_ms=rms_run_step_time_ms(run),
+    num, _, _ = rms_read_partials(run)
+    res = dict(S=S, num=num, moments=mom, alpha_sum=asum, status=seq.status, step_ms=rms_run_step_time_ms(run),
                b_s=rms_sequence_bvalues(seq), leap_limit=run.status == L.RMS_W_LEAP_LIMIT)
     if walkers:
         res.update(rms_read_walkers(run))
@@ -318,14 +361,31 @@ def simulate(wl, precision: int = RMS_FP64, n_walkers: Optional[int] = None, see
     return res
 
 
+def rms_measure_peak(kind: int, volume_elems: int = 0, target_ms: float = 20.0, reps: int = 3,
+                     stream: Optional[int] = None):
+    """(rate per second, ms of the best launch) of one machine peak
+    (include/rms_peaks.h: RMS_PEAK_FP64_ADD/MUL/FMA, RMS_PEAK_GATHER[_DEP])."""
+    rate, ms = C.c_double(), C.c_double()
+    check(L.lib.rms_measure_peak(int(kind), int(volume_elems), float(target_ms), int(reps),
+                                 current_stream() if stream is None else stream, C.byref(rate), C.byref(ms)))
+    return float(rate.value), float(ms.value)
+
+
+def rms_device_sm_count() -> int:
+    n = C.c_int32()
+    check(L.lib.rms_device_sm_count(C.byref(n)))
+    return int(n.value)
+
+
 class Server:
     """The continuous-batching serving loop (rms_server_* in include/rms.h)."""
 
     STATS = ("p50_ms", "p99_ms", "mean_ms", "walker_steps_per_s", "completed", "in_flight", "queued",
              "peak_in_flight", "ticks", "graph_updates", "graph_instantiations")
 
-    def __init__(self, memory_budget_bytes: int = 0, max_active: int = 0, steps_per_tick: int = 0):
-        cfg = L.ServerConfig(int(memory_budget_bytes), int(max_active), int(steps_per_tick))
+    def __init__(self, memory_budget_bytes: int = 0, max_active: int = 0, steps_per_tick: int = 0,
+                 policy: int = L.RMS_SERVE_STEPS):
+        cfg = L.ServerConfig(int(memory_budget_bytes), int(max_active), int(steps_per_tick), int(policy))
         h = C.c_void_p()
         check(L.lib.rms_server_create(C.byref(cfg), C.byref(h)))
         self.handle = h
@@ -352,6 +412,12 @@ class Server:
                                     mom.ctypes.data if q.n_rec else None, asum.ctypes.data))
         del self._shapes[ticket]
         return (re + 1j * im).reshape(q.n_shapes, q.n_dirs, q.n_b), mom, float(asum[0])
+
+    def request_info(self, ticket: int) -> dict:
+        """Timing of a finished request (before wait() releases it)."""
+        out = np.zeros(4)
+        check(L.lib.rms_server_request_info(self.handle, ticket, out.ctypes.data))
+        return dict(queue_ms=out[0], latency_ms=out[1], walker_steps=out[2], ticks=int(out[3]))
 
     def cancel(self, ticket: int) -> None:
         check(L.lib.rms_server_cancel(self.handle, ticket))

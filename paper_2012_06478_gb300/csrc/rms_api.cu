@@ -403,13 +403,33 @@ __global__ void readout_reduce_kernel(const double *part, int32_t n_chunks, int3
     out[combo * 2 + 1] = is + ic;
 }
 
-__global__ void normalise_kernel(double *S, int32_t n_combo)
+// S = sum alpha e^{-i phi} / sum alpha from the unnormalised sums, which stay
+// as they are (rms_read_partials returns them for combining walker shards).
+__global__ void normalise_kernel(const double *sums, int32_t n_combo, double *S)
 {
     const int combo = blockIdx.x * blockDim.x + threadIdx.x;
-    if (combo >= n_combo) return;
-    const double asum = S[n_combo * 2];
-    S[combo * 2 + 0] = S[combo * 2 + 0] / asum;
-    S[combo * 2 + 1] = S[combo * 2 + 1] / asum;
+    if (combo > n_combo) return;
+    const double asum = sums[n_combo * 2];
+    if (combo == n_combo) {
+        S[combo * 2 + 0] = asum;
+        S[combo * 2 + 1] = 0.0;
+        return;
+    }
+    S[combo * 2 + 0] = sums[combo * 2 + 0] / asum;
+    S[combo * 2 + 1] = sums[combo * 2 + 1] / asum;
+}
+
+// The counter-based generator, one thread per (counter, key) pair.
+__global__ void philox_words_kernel(const uint32_t *ctr, const uint32_t *key, int64_t n, uint32_t *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const U4 r = philox4x32_10(U4{ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]}, key[2 * i],
+                               key[2 * i + 1]);
+    out[4 * i] = r.x;
+    out[4 * i + 1] = r.y;
+    out[4 * i + 2] = r.z;
+    out[4 * i + 3] = r.w;
 }
 
 // Final per-walker state in array-of-structures form, FP64.
@@ -956,7 +976,7 @@ static rms_status finalize_impl(rms_run_handle *r)
                                                     q->d_dirs, q->n_dirs, q->n_b, r->n_combo, r->d_ro_partial);
     readout_reduce_kernel<<<(r->n_combo + 1 + 127) / 128, 128, 0, s>>>(r->d_ro_partial, r->n_chunks, r->n_combo,
                                                                        r->d_S);
-    normalise_kernel<<<(r->n_combo + 127) / 128, 128, 0, s>>>(r->d_S, r->n_combo);
+    normalise_kernel<<<(r->n_combo + 1 + 127) / 128, 128, 0, s>>>(r->d_S, r->n_combo, normalised_S(r));
     RMS_CUDA(cudaGetLastError());
     return RMS_OK;
 }
@@ -991,7 +1011,7 @@ size_t rms::run_state_bytes(const rms_sequence *q, int64_t W, int32_t precision,
     size_t b = precision == RMS_FP32 ? layout_state<float>(s32, nullptr, W, q->S, hash, true, cnt)
                                      : layout_state<double>(s64, nullptr, W, q->S, hash, false, cnt);
     b += sizeof(double) * ((size_t)std::max(q->n_rec, 1) * nb * kMoments + (size_t)std::max(q->n_rec, 1) * kMoments +
-                           2 * (size_t)(ncombo + 1) * nc + 2 * (size_t)(ncombo + 1));
+                           2 * (size_t)(ncombo + 1) * nc + 4 * (size_t)(ncombo + 1));
     return b;
 }
 
@@ -1019,7 +1039,7 @@ rms_status rms::run_setup(rms_run_handle *r, bool with_cancel_and_events)
     RMS_CUDA(cudaMemsetAsync(r->d_mom_partial, 0, sizeof(double) * nmp, s));
     RMS_CUDA(cudaMallocAsync((void **)&r->d_mom, sizeof(double) * std::max(q->n_rec, 1) * kMoments, s));
     RMS_CUDA(cudaMallocAsync((void **)&r->d_ro_partial, sizeof(double) * 2 * (size_t)(r->n_combo + 1) * r->n_chunks, s));
-    RMS_CUDA(cudaMallocAsync((void **)&r->d_S, sizeof(double) * 2 * (r->n_combo + 1), s));
+    RMS_CUDA(cudaMallocAsync((void **)&r->d_S, sizeof(double) * 4 * (r->n_combo + 1), s));
     RMS_CUDA(cudaMallocAsync((void **)&r->d_status, sizeof(int32_t), s));
     RMS_CUDA(cudaMemsetAsync(r->d_status, 0, sizeof(int32_t), s));
     if (with_cancel_and_events) {
@@ -1227,7 +1247,7 @@ extern "C" rms_status rms_read_signal(rms_run_handle *r, double *S_re, double *S
     const rms_status fin = finish(r);
     if (fin < 0) return fin;
     std::vector<double> S((size_t)2 * (r->n_combo + 1));
-    RMS_CUDA(cudaMemcpy(S.data(), r->d_S, sizeof(double) * S.size(), cudaMemcpyDeviceToHost));
+    RMS_CUDA(cudaMemcpy(S.data(), normalised_S(r), sizeof(double) * S.size(), cudaMemcpyDeviceToHost));
     for (int k = 0; k < r->n_combo; ++k) {
         if (S_re) S_re[k] = S[2 * k];
         if (S_im) S_im[k] = S[2 * k + 1];
@@ -1236,6 +1256,48 @@ extern "C" rms_status rms_read_signal(rms_run_handle *r, double *S_re, double *S
     if (moments && r->seq->n_rec > 0)
         RMS_CUDA(cudaMemcpy(moments, r->d_mom, sizeof(double) * r->seq->n_rec * kMoments, cudaMemcpyDeviceToHost));
     return fin;
+}
+
+extern "C" rms_status rms_read_partials(rms_run_handle *r, double *num_re, double *num_im, double *alpha_sum,
+                                        double *moments)
+{
+    if (!r) return fail(RMS_E_INVALID_ARG, "null run");
+    const rms_status fin = finish(r);
+    if (fin < 0) return fin;
+    std::vector<double> S((size_t)2 * (r->n_combo + 1));
+    RMS_CUDA(cudaMemcpy(S.data(), r->d_S, sizeof(double) * S.size(), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < r->n_combo; ++k) {
+        if (num_re) num_re[k] = S[2 * k];
+        if (num_im) num_im[k] = S[2 * k + 1];
+    }
+    if (alpha_sum) *alpha_sum = S[2 * r->n_combo];
+    if (moments && r->seq->n_rec > 0)
+        RMS_CUDA(cudaMemcpy(moments, r->d_mom, sizeof(double) * r->seq->n_rec * kMoments, cudaMemcpyDeviceToHost));
+    return fin;
+}
+
+extern "C" rms_status rms_normalise_partials(int64_t n_combo, const double *num_re, const double *num_im,
+                                             double alpha_sum, double *S_re, double *S_im)
+{
+    if (n_combo < 0 || (n_combo > 0 && (!num_re || !num_im || !S_re || !S_im)))
+        return fail(RMS_E_INVALID_ARG, "rms_normalise_partials: n_combo >= 0 and non-null arrays");
+    for (int64_t k = 0; k < n_combo; ++k) {
+        S_re[k] = num_re[k] / alpha_sum;
+        S_im[k] = num_im[k] / alpha_sum;
+    }
+    return RMS_OK;
+}
+
+extern "C" rms_status rms_philox4x32_10(const uint32_t *ctr, const uint32_t *key, int64_t n, uint32_t *out,
+                                        void *stream)
+{
+    if (n < 0 || (n > 0 && (!ctr || !key || !out))) return fail(RMS_E_INVALID_ARG, "rms_philox4x32_10: bad arguments");
+    if (n == 0) return RMS_OK;
+    const int64_t blocks = (n + 255) / 256;
+    if (blocks > 0x7FFFFFFF) return fail(RMS_E_INVALID_ARG, "rms_philox4x32_10: n too large");
+    philox_words_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(ctr, key, n, out);
+    RMS_CUDA(cudaGetLastError());
+    return RMS_OK;
 }
 
 extern "C" rms_status rms_read_walkers(rms_run_handle *r, int32_t *i, double *o, int32_t *i0, double *o0, int32_t *c,

@@ -75,7 +75,9 @@ struct rms_run_handle {
     rms::WalkerState<double> st64{};
     rms::WalkerState<float> st32{};
     double *d_mom_partial = nullptr, *d_mom = nullptr;
-    double *d_ro_partial = nullptr, *d_S = nullptr;  // S: [combo][2] + alpha sum
+    // d_S: the unnormalised sums [combo][2] + (alpha sum, 0), then the
+    // normalised signal in the same layout (normalised_S)
+    double *d_ro_partial = nullptr, *d_S = nullptr;
     int32_t *d_status = nullptr;
     int32_t *h_cancel = nullptr, *d_cancel = nullptr;
     cudaEvent_t ev_start = nullptr, ev_end = nullptr;
@@ -101,6 +103,9 @@ rms_status fail(rms_status st, const std::string &msg);
         rms_status st_ = (expr); \
         if (st_ < 0) return st_; \
     } while (0)
+
+// The normalised signal [combo][2] + (alpha sum, 0) of a finalised run.
+inline double *normalised_S(const rms_run_handle *r) { return r->d_S + 2 * (size_t)(r->n_combo + 1); }
 
 template <typename Real>
 size_t layout_state(WalkerState<Real> &st, char *base, int64_t W, int S, bool hash, bool f32, bool counts);

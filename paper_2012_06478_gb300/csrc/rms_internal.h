@@ -38,6 +38,11 @@ extern template cudaError_t launch_walk_batched<double>(int, int32_t, cudaStream
 extern template cudaError_t launch_walk_batched<float>(int, int32_t, cudaStream_t, const ReqDesc<float> *,
                                                        const BlockTask *);
 
+template <typename Real>
+int batched_blocks_per_sm(int ns_bucket);
+extern template int batched_blocks_per_sm<double>(int);
+extern template int batched_blocks_per_sm<float>(int);
+
 int walk_block_size();
 
 // Message returned by rms_last_error() on the calling thread.

@@ -56,7 +56,8 @@ struct Request {
     bool cancel = false;
     rms_status err = RMS_OK;
     std::string msg;
-    Clock::time_point t_submit, t_done;
+    Clock::time_point t_submit, t_admit, t_done;
+    int64_t ticks = 0;  // ticks the request took part in
     double *h_out = nullptr;  // pinned: S [2*(n_combo+1)], moments [n_rec*22], status word
     size_t h_out_bytes = 0;
     cudaEvent_t done_ev = nullptr;
@@ -94,6 +95,8 @@ struct rms_server {
     cudaGraphExec_t exec = nullptr;
     std::atomic<int64_t> graph_updates{0}, graph_instantiations{0};
     std::vector<std::pair<double *, size_t>> pinned_pool;
+    // block slots of the batched kernel: [precision: 0 FP32, 1 FP64][shape bucket]
+    int64_t slots[2][4] = {};
     // statistics
     std::vector<double> lat_ms;
     std::atomic<double> walker_steps{0.0};  // scheduler thread only (see tick)
@@ -227,6 +230,7 @@ void admit(rms_server *s)
         s->active.push_back(q);
         publish_in_flight(s);
         std::lock_guard<std::mutex> lk(s->mu);
+        q->t_admit = Clock::now();
         q->st = St::Active;
         s->peak_active = std::max<int>(s->peak_active, (int)(s->active.size() + s->finalizing.size()));
     }
@@ -275,12 +279,23 @@ rms_status tick_once(rms_server *s)
     for (int g = 0; g < 8; ++g) {  // groups: precision x shape bucket
         const int prec = g / 4 == 0 ? RMS_FP32 : RMS_FP64;
         start[g] = off;
+        // RMS_SERVE_FILL: the launch of this group lasts `waves` x steps_per_tick
+        // block-steps (its blocks over the GPU's block slots); requests whose
+        // blocks fit in one wave take that many steps
+        int64_t blocks = 0;
+        for (Request *q : s->active)
+            if (q->precision == prec && bucket_index(q->bucket) == g % 4) blocks += q->run->n_blocks;
+        const int64_t slots = s->slots[g / 4][g % 4];
+        const int64_t waves = std::min<int64_t>(64, std::max<int64_t>(1, blocks / std::max<int64_t>(slots, 1)));
         for (size_t i = 0; i < s->active.size(); ++i) {
             Request *q = s->active[i];
             if (q->precision != prec || bucket_index(q->bucket) != g % 4) continue;
+            int64_t quota = s->cfg.steps_per_tick;
+            if (s->cfg.policy == RMS_SERVE_FILL && q->run->n_blocks < slots) quota *= waves;
             const int64_t k0 = q->progress;
-            const int64_t k1 = std::min<int64_t>(q->seq->n_steps, k0 + s->cfg.steps_per_tick);
+            const int64_t k1 = std::min<int64_t>(q->seq->n_steps, k0 + quota);
             range[i] = {k0, k1};
+            ++q->ticks;
             for (int64_t b = 0; b < q->run->n_blocks; ++b) T[off++] = BlockTask{q->slot, 0, b, k0, k1};
         }
         count[g] = off - start[g];
@@ -328,7 +343,8 @@ rms_status tick_once(rms_server *s)
             rms_run_handle *r = q->run;
             RMS_TRY(run_finalize(r));
             const size_t nS = 2 * (size_t)(r->n_combo + 1);
-            RMS_CUDA(cudaMemcpyAsync(q->h_out, r->d_S, sizeof(double) * nS, cudaMemcpyDeviceToHost, s->stream));
+            RMS_CUDA(cudaMemcpyAsync(q->h_out, normalised_S(r), sizeof(double) * nS, cudaMemcpyDeviceToHost,
+                                     s->stream));
             if (q->seq->n_rec > 0)
                 RMS_CUDA(cudaMemcpyAsync(q->h_out + nS, r->d_mom, sizeof(double) * q->seq->n_rec * kMoments,
                                          cudaMemcpyDeviceToHost, s->stream));
@@ -459,7 +475,8 @@ extern "C" rms_status rms_server_create(const rms_server_config *cfg, rms_server
     if (!out) return fail(RMS_E_INVALID_ARG, "null argument");
     *out = nullptr;
     rms_server_config c = cfg ? *cfg : rms_server_config{};
-    if (c.memory_budget_bytes < 0 || c.max_active < 0 || c.max_active > 1024 || c.steps_per_tick < 0)
+    if (c.memory_budget_bytes < 0 || c.max_active < 0 || c.max_active > 1024 || c.steps_per_tick < 0 ||
+        (c.policy != RMS_SERVE_STEPS && c.policy != RMS_SERVE_FILL))
         return fail(RMS_E_INVALID_ARG, "server config out of range");
     if (c.memory_budget_bytes == 0) c.memory_budget_bytes = 8ll << 30;
     if (c.max_active == 0) c.max_active = 64;
@@ -468,6 +485,12 @@ extern "C" rms_status rms_server_create(const rms_server_config *cfg, rms_server
     if (!s) return fail(RMS_E_OOM, "host allocation");
     s->cfg = c;
     cudaGetDevice(&s->device);
+    int sms = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    for (int b = 0; b < 4; ++b) {
+        s->slots[0][b] = (int64_t)sms * batched_blocks_per_sm<float>(1 << b);
+        s->slots[1][b] = (int64_t)sms * batched_blocks_per_sm<double>(1 << b);
+    }
     auto bail = [&](cudaError_t e) {
         rms_status st = fail(e == cudaErrorMemoryAllocation ? RMS_E_OOM : RMS_E_CUDA, cudaGetErrorString(e));
         if (s->stream) cudaStreamDestroy(s->stream);
@@ -565,6 +588,23 @@ extern "C" rms_status rms_server_wait(rms_server *s, int64_t ticket, int64_t tim
     s->reqs.erase(it);
     delete q;
     return st;
+}
+
+extern "C" rms_status rms_server_request_info(rms_server *s, int64_t ticket, double *out)
+{
+    if (!s || !out) return fail(RMS_E_INVALID_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(RMS_E_INVALID_ARG, "unknown ticket");
+    const Request *q = it->second;
+    if (q->st != St::Done) return q->st == St::Failed || q->st == St::Cancelled
+                                      ? fail(RMS_E_INVALID_ARG, "the request did not complete")
+                                      : RMS_E_NOT_READY;
+    out[0] = std::chrono::duration<double, std::milli>(q->t_admit - q->t_submit).count();
+    out[1] = std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count();
+    out[2] = (double)q->W * (double)q->seq->n_steps;
+    out[3] = (double)q->ticks;
+    return RMS_OK;
 }
 
 extern "C" rms_status rms_server_cancel(rms_server *s, int64_t ticket)

@@ -19,6 +19,7 @@
 #include <type_traits>
 
 #include "rms_device.cuh"
+#include "soft_fp64.cuh"
 
 namespace rms {
 
@@ -83,6 +84,38 @@ __device__ __forceinline__ void octant_map(uint32_t oct, double cs, double sn, d
     sy = negy ? -b : b;
 }
 
+// The hardware FP64 operations, for the operands the integer-ALU versions
+// hand back (zeros, subnormals, out-of-range results).  Out of line, so that
+// the compiler cannot evaluate them speculatively beside the integer path:
+// inlined, a predicated copy would run on the FP64 pipe at every call.
+static __device__ __noinline__ double hw_mul(double a, double b) { return a * b; }
+static __device__ __noinline__ double hw_div(double a, double b) { return a / b; }
+static __device__ __noinline__ double hw_sqrt(double x) { return sqrt(x); }
+
+// FP64 products, quotients of non-negative operands and square roots on the
+// integer ALU (sfp::mul_rn, div_pos, sqrt_pos: the IEEE results bit for bit).
+// mulr is the product of the form: this one for FP64, a plain multiply for FP32.
+__device__ __forceinline__ double dmul(double a, double b)
+{
+    double p;
+    if (!sfp::mul_rn(a, b, p)) p = hw_mul(a, b);
+    return p;
+}
+__device__ __forceinline__ double ddiv_nn(double a, double b)
+{
+    double q;
+    if (!sfp::div_pos(a, b, q)) q = hw_div(a, b);
+    return q;
+}
+__device__ __forceinline__ double dsqrt(double x)
+{
+    double r;
+    if (!sfp::sqrt_pos(x, r)) r = hw_sqrt(x);
+    return r;
+}
+__device__ __forceinline__ double mulr(double a, double b) { return dmul(a, b); }
+__device__ __forceinline__ float mulr(float a, float b) { return a * b; }
+
 // Exact doubles built from their bits on the integer ALU, so that values
 // which need no rounding do not occupy GB300's narrow FP64 pipe.
 // k * 2^e2 for an odd |k| < 2^32: no rounding, the same bits as converting k
@@ -126,7 +159,7 @@ __device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, const d
     const bool zneg = x0 >= 0x80000000u;
     const uint32_t kmag = zneg ? 2u * x0 + 1u : 0xFFFFFFFFu - 2u * x0;  // |k|
     const double z = odd_scaled(kmag, zneg, -32);
-    const double r = sqrt(u64_scaled_rn(0ULL - (unsigned long long)kmag * kmag));
+    const double r = dsqrt(u64_scaled_rn(0ULL - (unsigned long long)kmag * kmag));  // argument in (2^-32, 1]
     const uint32_t oct = x1 >> 29;
     uint32_t m = x1 & 0x1FFFFFFFu;
     if (oct & 1u) m = 0x1FFFFFFFu - m;
@@ -135,17 +168,17 @@ __device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, const d
     const uint32_t j = m >> 19;
     const int32_t lo = (int32_t)(m & 0x7FFFFu);
     const int32_t e_int = 2 * lo + 1 - (1 << 19);  // odd
-    const double e = odd_scaled((uint32_t)(e_int < 0 ? -e_int : e_int), e_int < 0, -30) * 0.78539816339744830962;
-    const double t = e * e;
-    const double se = e + (e * t) * (-1.0 / 6.0 + t * (1.0 / 120.0));
-    const double ce = 1.0 + t * (-1.0 / 2.0 + t * (1.0 / 24.0));
+    const double e = dmul(odd_scaled((uint32_t)(e_int < 0 ? -e_int : e_int), e_int < 0, -30), 0.78539816339744830962);
+    const double t = dmul(e, e);
+    const double se = e + dmul(dmul(e, t), -1.0 / 6.0 + dmul(t, 1.0 / 120.0));
+    const double ce = 1.0 + dmul(t, -1.0 / 2.0 + dmul(t, 1.0 / 24.0));
     const double cj = __ldg(trig + 2 * j), sj = __ldg(trig + 2 * j + 1);
-    const double cs = cj * ce - sj * se;
-    const double sn = sj * ce + cj * se;
+    const double cs = dmul(cj, ce) - dmul(sj, se);
+    const double sn = dmul(sj, ce) + dmul(cj, se);
     double cx, sy;
     octant_map(oct, cs, sn, cx, sy);
-    n[0] = r * cx;
-    n[1] = r * sy;
+    n[0] = dmul(r, cx);
+    n[1] = dmul(r, sy);
     n[2] = z;
 }
 
@@ -268,6 +301,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
     const int32_t stride[3] = {1, g.nx, g.nx * g.ny};
     const int32_t per[3] = {g.per_x, g.per_y, g.per_z};
     const int32_t L = t.n_labels;
+    const Real lp = (Real)g.voxel_um;  // voxel edge in the form's precision, converted once
 
     Real o[3], o0[3];
     int32_t di[3], wc[3];
@@ -356,7 +390,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
             Real sc = __ldg(t.s + c);
             Real rate = t.any_relax ? __ldg(t.dtR + mode * L + c) : Real(0);
             [[maybe_unused]] const Real rate0 = rate;
-            Real d[3] = {n[0] * sc, n[1] * sc, n[2] * sc};
+            Real d[3] = {mulr(n[0], sc), mulr(n[1], sc), mulr(n[2], sc)};
             [[maybe_unused]] bool refused = false;
             // A face event on axis `best` moving up/down: look up the voxel across
             // it and decide between crossing and reflection.
@@ -455,13 +489,15 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                 // Plain form: the CPU FP64 reference's operation order; comparisons on the
                 // integer ALU (dgt0/dlt_nn/dclamp01 give the IEEE results).
                 const double kInf = __longlong_as_double(0x7FF0000000000000LL);
-                // one division per axis: (1 - o)/d moving up, o/(-d) moving down
+                // one division per axis: (1 - o)/d moving up, o/(-d) moving down, on the
+                // integer ALU (the IEEE quotient; the hardware division only for operands
+                // outside its range, e.g. o = -0)
                 double T[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     const double num = dgt0(d[a]) ? 1.0 - o[a] : o[a];
                     const double den = __longlong_as_double(dbits(d[a]) & 0x7FFFFFFFFFFFFFFFLL);  // |d|
-                    T[a] = (dgt0(d[a]) || dlt0(d[a])) ? num / den : kInf;
+                    T[a] = (dgt0(d[a]) || dlt0(d[a])) ? ddiv_nn(num, den) : kInf;
                 }
                 double tau = 0.0;
 #pragma unroll  // unrolled: each event index is a constant (measured 5 % faster, FP32)
@@ -486,10 +522,10 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                             o[a] = up ? 1.0 : 0.0;
                             T[a] = kInf;
                         } else {
-                            o[a] = dclamp01(o[a] + dts * d[a]);
+                            o[a] = dclamp01(o[a] + dmul(dts, d[a]));
                         }
                     }
-                    if (t.any_relax) A = A + dts * rate;
+                    if (t.any_relax) A = A + dmul(dts, rate);
                     tau = tmin;
                     if constexpr (HASH) ++nev;
                     const bool changed = face(best, up, ev);
@@ -502,10 +538,10 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                             sc = sn;
 #pragma unroll
                             for (int a = 0; a < 3; ++a) {
-                                d[a] = n[a] * sc;
+                                d[a] = dmul(n[a], sc);
                                 if (dbits(T[a]) == 0x7FF0000000000000LL) continue;
                                 const double num = dgt0(d[a]) ? 1.0 - o[a] : o[a];
-                                T[a] = tau + num / __longlong_as_double(dbits(d[a]) & 0x7FFFFFFFFFFFFFFFLL);
+                                T[a] = tau + ddiv_nn(num, __longlong_as_double(dbits(d[a]) & 0x7FFFFFFFFFFFFFFFLL));
                             }
                         }
                     }
@@ -513,8 +549,8 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                 if (IM == kInteractEC || !refused) {
                     const double rem = 1.0 - tau;
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) o[a] = dclamp01(o[a] + rem * d[a]);
-                    if (t.any_relax) A = A + rem * rate;
+                    for (int a = 0; a < 3; ++a) o[a] = dclamp01(o[a] + dmul(rem, d[a]));
+                    if (t.any_relax) A = A + dmul(rem, rate);
                 }
             } else {
                 // Precision form: the same walk in FP32 (approximate division).
@@ -638,7 +674,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                 Real dx[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
-                    dx[a] = (Real)g.voxel_um * ((Real)di[a] + (o[a] - o0[a]));
+                    dx[a] = mulr(lp, (Real)di[a] + (o[a] - o0[a]));
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
                     if (s < ctl.n_shapes) {
@@ -646,7 +682,7 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
                             if (kF64)
-                                ph[s][a] = ph[s][a] + wg * dx[a];
+                                ph[s][a] = ph[s][a] + dmul(wg, dx[a]);
                             else
                                 kahan_add(ph[s][a], phc[s][a], wg * dx[a]);
                         }
@@ -747,6 +783,24 @@ cudaError_t launch_walk_batched(int ns_bucket, int32_t n_tasks, cudaStream_t str
     else
         walk_batched_kernel<Real, 8><<<grid, kWalkBlock, 0, stream>>>(reqs, tasks, n_tasks);
     return cudaGetLastError();
+}
+
+// Resident blocks per SM of the batched kernel (the serving scheduler's
+// count of block slots).
+template <typename Real>
+int batched_blocks_per_sm(int ns_bucket)
+{
+    int n = 0;
+    cudaError_t e;
+    if (ns_bucket <= 1)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_batched_kernel<Real, 1>, kWalkBlock, 0);
+    else if (ns_bucket <= 2)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_batched_kernel<Real, 2>, kWalkBlock, 0);
+    else if (ns_bucket <= 4)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_batched_kernel<Real, 4>, kWalkBlock, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_batched_kernel<Real, 8>, kWalkBlock, 0);
+    return e == cudaSuccess && n > 0 ? n : 1;
 }
 
 // Host-side launcher for interaction IM and absorbing membranes MT,

@@ -21,19 +21,23 @@ def shard_range(rank: int, world: int, n_walkers: int, weak: bool = False):
     return (n_walkers * rank) // world, (n_walkers * (rank + 1)) // world
 
 
-def pack_partials(S: np.ndarray, alpha_sum: float, moments: np.ndarray) -> np.ndarray:
-    """One rank's reducible sums as a flat FP64 vector: alpha-weighted signal
-    numerators (S * sum alpha), sum alpha, moment sums."""
-    num = np.asarray(S, np.complex128).ravel() * alpha_sum
+def pack_partials(num: np.ndarray, alpha_sum: float, moments: np.ndarray) -> np.ndarray:
+    """One rank's reducible sums as a flat FP64 vector, exactly as the library
+    returns them (rms_read_partials): the signal numerators sum alpha
+    e^{-i phi}, sum alpha, the moment sums."""
+    num = np.asarray(num, np.complex128).ravel()
     return np.concatenate([num.real, num.imag, [alpha_sum], np.asarray(moments, np.float64).ravel()])
 
 
 def unpack_partials(v: np.ndarray, S_shape, m_shape):
+    """(S, moments, sum alpha) from a merged vector; S = numerators / sum alpha
+    is computed by the library (rms_normalise_partials)."""
+    from .api import rms_normalise_partials
     n = int(np.prod(S_shape))
-    num = v[:n] + 1j * v[n:2 * n]
+    num = (v[:n] + 1j * v[n:2 * n]).reshape(S_shape)
     asum = float(v[2 * n])
     mom = v[2 * n + 1:].reshape(m_shape)
-    return (num / asum).reshape(S_shape), mom, asum
+    return rms_normalise_partials(num, asum), mom, asum
 
 
 def merge_in_rank_order(parts) -> np.ndarray:

@@ -24,7 +24,8 @@ import numpy as np
 __all__ = [
     "Workload", "cylinder_labels", "slab_labels", "box_labels", "axon_labels",
     "voronoi_labels", "pgse", "ogse", "fibonacci_dirs", "axis_dirs",
-    "uniform_tables", "workload", "WORKLOADS", "serving_requests",
+    "uniform_tables", "workload", "WORKLOADS", "serving_requests", "serving_geometry", "serving_tables",
+    "SERVING_GEOMETRIES",
 ]
 
 
@@ -383,6 +384,54 @@ def workload(name: str) -> Workload:
 
 # ---------------------------------------------------------------- serving load
 
+SERVING_GEOMETRIES = 2  # label volumes per (kind, size) in the serving pool
+
+
+def serving_geometry(kind: str, n: int, geometry_seed: int) -> np.ndarray:
+    """Label volume of a serving request: the cylinder, axon or Voronoi
+    generator at n^3 with 0.1 um voxels (axons at the 200-axon workload's
+    areal density, Voronoi cells at the 512^3 workload's cell density)."""
+    rng = np.random.default_rng(1000 * n + geometry_seed)
+    if kind == "cylinder":
+        return cylinder_labels(n, n * rng.uniform(0.2, 0.4))
+    if kind == "axons":
+        return axon_labels(n, n, n, 0.1, max(2, int(round(200 * (n / 200.0) ** 2))), seed=40 + n + 7 * geometry_seed)
+    return voronoi_labels(n, max(8, int(1000 * (n / 512.0) ** 3)), seed=50 + n + 7 * geometry_seed)
+
+
+def serving_tables(kind: str, n_labels: int, params_seed: int):
+    """Per-label tissue tables of a serving request, drawn per request by the
+    recipe of its generator's workload: the cylinder with D ~ U(0.5, 2.5) per
+    label, kappa log-uniform 0.005-0.05 um/ms, T2 ~ U(40, 100) ms; axons with
+    D_in = 2, D_ex = 1.5, per-axon kappa log-uniform 0.005-0.05 (two
+    membranes in series between axons), T2 60 / 40 ms; Voronoi cells with
+    D ~ U(0.5, 2.5), per-pair kappa ~ U(0, 0.05), T1 ~ U(600, 1000),
+    T2 ~ U(40, 100) ms.  Returns D, T2, T1, kappa (L, L)."""
+    rng = np.random.default_rng(params_seed)
+    L = n_labels
+    T1 = np.full(L, math.inf)
+    if kind == "cylinder":
+        D = rng.uniform(0.5, 2.5, size=L)
+        T2 = rng.uniform(40, 100, size=L)
+        K = np.full((L, L), math.exp(rng.uniform(math.log(0.005), math.log(0.05))))
+    elif kind == "axons":
+        D = np.full(L, 2.0)
+        D[0] = 1.5
+        T2 = np.full(L, 60.0)
+        T2[0] = 40.0
+        k = np.concatenate([[math.inf], np.exp(rng.uniform(math.log(0.005), math.log(0.05), size=L - 1))])
+        with np.errstate(divide="ignore"):
+            K = 1.0 / (1.0 / k[:, None] + 1.0 / k[None, :])
+    else:
+        D = rng.uniform(0.5, 2.5, size=L)
+        T1 = rng.uniform(600, 1000, size=L)
+        T2 = rng.uniform(40, 100, size=L)
+        K = np.triu(rng.uniform(0.0, 0.05, size=(L, L)), 1)
+        K = K + K.T
+    np.fill_diagonal(K, 0.0)
+    return D, T2, T1, K
+
+
 def serving_requests(n: int, seed: int, sizes=(32, 64, 128, 256), walkers=(1e4, 1e6),
                      steps=(1e3, 5e4), dirs=(6, 64)):
     """A seeded stream of simulation requests: each a substrate kind from
@@ -398,5 +447,6 @@ def serving_requests(n: int, seed: int, sizes=(32, 64, 128, 256), walkers=(1e4, 
             n_steps=int(round(math.exp(rng.uniform(math.log(steps[0]), math.log(steps[1]))))),
             n_dirs=int(rng.integers(dirs[0], dirs[1] + 1)),
             seed=int(rng.integers(0, 2 ** 63 - 1)),
+            geometry=int(rng.integers(0, SERVING_GEOMETRIES)),
         ))
     return out

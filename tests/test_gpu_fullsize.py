@@ -142,8 +142,8 @@ def test_three_hundred_million_walkers(rms):
         full = rms.simulate(wl, prec)
         a = rms.simulate(wl, prec, n_walkers=W // 2)
         b = rms.simulate(wl, prec, n_walkers=W - W // 2, walker_begin=W // 2)
-        v = shard.merge_in_rank_order([shard.pack_partials(a["S"], a["alpha_sum"], a["moments"]),
-                                       shard.pack_partials(b["S"], b["alpha_sum"], b["moments"])])
+        v = shard.merge_in_rank_order([shard.pack_partials(a["num"], a["alpha_sum"], a["moments"]),
+                                       shard.pack_partials(b["num"], b["alpha_sum"], b["moments"])])
         S, M, asum = shard.unpack_partials(v, full["S"].shape, full["moments"].shape)
         np.testing.assert_allclose(S, full["S"], rtol=0, atol=1e-12)
         np.testing.assert_allclose(M, full["moments"], rtol=1e-12)

@@ -50,7 +50,8 @@ def _open(rms, wl):
     return sub, seq
 
 
-def test_requests_alone_and_in_the_mix(rms):
+@pytest.mark.parametrize("policy", [0, 1])
+def test_requests_alone_and_in_the_mix(rms, policy):
     cases = _cases()
     handles = [_open(rms, wl) for wl, _, _ in cases]
     jobs = []
@@ -60,7 +61,7 @@ def test_requests_alone_and_in_the_mix(rms):
             jobs.append((seq, W, seed, prec, rms.rms_read_signal(run)))
             run.close()
     # a budget that holds only part of the requests at once: the rest queue
-    srv = rms.Server(memory_budget_bytes=12 << 20, max_active=4, steps_per_tick=64)
+    srv = rms.Server(memory_budget_bytes=12 << 20, max_active=4, steps_per_tick=64, policy=policy)
     tickets = [srv.submit(seq, W, seed, prec) for seq, W, seed, prec, _ in jobs]
     tickets += [srv.submit(seq, W, seed, prec) for seq, W, seed, prec, _ in jobs]  # the same again
     results = [srv.wait(t, timeout_ms=120000) for t in tickets]
@@ -82,6 +83,39 @@ def test_requests_alone_and_in_the_mix(rms):
     for sub, seq in handles:
         seq.close()
         sub.close()
+
+
+def test_size_aware_policy_lets_small_requests_fill_the_tick(rms):
+    """RMS_SERVE_FILL: next to a request whose blocks span several waves of
+    the GPU, a small request advances several waves' worth of steps per tick
+    (fewer ticks than steps / steps_per_tick), with the same result as alone;
+    under RMS_SERVE_STEPS it takes one tick per steps_per_tick steps."""
+    import rms_inputs as ri
+    n = 4096
+    big = ri.workload("cylinder-32^3").with_(n_steps=n, G=ri.pgse(0.5, 1.0, 1e-3, n)[None, :],
+                                             rec_steps=np.array([n]))
+    sub, seq = _open(rms, big)
+    W_big, W_small = 1_200_000, 2000   # > 6 waves of 128-walker blocks on 152 SMs x 8 slots; one block row
+    ref = rms.rms_run(seq, W_small, 77, rms.RMS_FP32)
+    S0, M0, a0 = rms.rms_read_signal(ref)
+    ref.close()
+    ticks = {}
+    for policy in (rms.RMS_SERVE_STEPS, rms.RMS_SERVE_FILL):
+        srv = rms.Server(max_active=4, steps_per_tick=128, policy=policy)
+        tb = srv.submit(seq, W_big, 5, rms.RMS_FP32)
+        ts = srv.submit(seq, W_small, 77, rms.RMS_FP32)
+        while not srv.poll(ts):
+            pass
+        ticks[policy] = srv.request_info(ts)["ticks"]
+        S, M, a = srv.wait(ts)
+        np.testing.assert_allclose(S, S0, rtol=0, atol=1e-6)
+        np.testing.assert_allclose(M, M0, rtol=1e-6)
+        srv.wait(tb)
+        srv.close()
+    assert ticks[rms.RMS_SERVE_STEPS] == n // 128
+    assert ticks[rms.RMS_SERVE_FILL] <= n // 128 // 2, ticks
+    seq.close()
+    sub.close()
 
 
 def test_cancel_and_busy(rms):

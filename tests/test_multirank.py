@@ -38,7 +38,9 @@ def _rank(rank, world, port, out_dir, weak):
     b, e = shard.shard_range(rank, world, wl.n_walkers, weak=weak)
     r = oracle.run(wl, b, e, n_threads=2)
     S, asum = oracle.readout(r, wl)
-    v = shard.allreduce_partials(shard.pack_partials(S, asum, r["moments"]))
+    # the oracle normalises; its numerators are S * sum alpha (the library
+    # returns them as such, rms_read_partials)
+    v = shard.allreduce_partials(shard.pack_partials(S * asum, asum, r["moments"]))
     Sm, Mm, am = shard.unpack_partials(v, S.shape, r["moments"].shape)
     np.savez(os.path.join(out_dir, f"rank{rank}.npz"), S=Sm, M=Mm, a=am, i=r["i"], o=r["o"], b=b, e=e)
     dist.barrier()
