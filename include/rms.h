@@ -415,9 +415,13 @@ rms_status rms_philox4x32_10(const uint32_t *ctr, const uint32_t *key, int64_t n
  * The work is enqueued on `stream` (cudaStream_t) and the call returns
  * without waiting.  It calls no cudaMalloc, cudaFree or other allocating
  * routine: its scratch is a fixed RMS_NOALLOC_SCRATCH_BYTES array inside the
- * library, present on every GPU that loads the library until the process
- * exits.  The first call on each device looks up that array's address (do it
- * before any stream capture on that device).  All calls share the array:
+ * library.  The CUDA runtime takes the array's memory on a device when it
+ * loads the library's device code there -- lazily, at the library's first
+ * use on that device, which may be this call -- and holds it until the
+ * process exits.  The first call on each device also looks up the array's
+ * address: make it (a warm-up call) before any stream capture on that
+ * device.  After the device's context is replaced (cudaDeviceReset) the next
+ * call loads the code and looks the address up again.  All calls share the array:
  * calls that may overlap on the GPU (other streams, other host threads) must
  * be serialised by the caller.  Errors: RMS_E_INVALID_ARG (null pointer,
  * n_walkers < 1, n_shapes outside 1..8, or 2*(n_shapes*n_dirs*n_b + 1) doubles

@@ -10,15 +10,21 @@
 // asking the driver for memory.
 //
 // How: the per-chunk partial sums live in one file-scope __device__ array of
-// fixed size (RMS_NOALLOC_SCRATCH_BYTES), loaded with the library and held by
-// every GPU that loads it until the process exits.  Host code cannot use the
-// array's name as a device address, so the first call on each device looks up
-// the address with cudaGetSymbolAddress (with that device current) and caches
-// it; that first call should therefore happen before any stream capture.
+// fixed size (RMS_NOALLOC_SCRATCH_BYTES).  The CUDA runtime loads the
+// library's device code on a device lazily, at its first use there, and the
+// array's memory is taken then and held until the process exits.  Host code
+// cannot use the array's name as a device address, so the first call on each
+// device looks up the address with cudaGetSymbolAddress (with that device
+// current) and caches it with the identity of the device's current context;
+// that first call should therefore happen before any stream capture.  A new
+// context on the device (after cudaDeviceReset, say) has a new copy of the
+// array at a new address: the next call sees the changed context identity
+// and looks the address up again.
 // Every call shares the array and it keeps the last call's contents: each
 // call writes every partial it later reads, so nothing needs clearing, but
 // calls that overlap on the GPU (different streams, or different host
 // threads on the same device) race on it and must be serialised by the caller.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -35,6 +41,35 @@ static __device__ __align__(256) double g_scratch[kScratchDoubles];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double *g_ptr[kMaxDevices] = {};
+unsigned long long g_ctx[kMaxDevices] = {};  // context identity the address belongs to
+
+// The driver's identity of the calling thread's current context (0 if it
+// cannot be had), through the runtime's driver entry points so that the
+// library needs no link to the driver library.
+unsigned long long current_context_id()
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (GetCurrent)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (GetId)f;
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 
 constexpr int kBlock = 128;
 constexpr int kTile = 64;
@@ -130,7 +165,10 @@ __global__ void noalloc_reduce_kernel(const double *part, int64_t n_chunks, int3
     if (combo == 0 && alpha_sum) *alpha_sum = a;
 }
 
-// The scratch array's device address on the current device (set up once).
+// The scratch array's device address on the current device: looked up once
+// per device and context (the first call, and again after the device's
+// context has changed; a context whose identity cannot be read is looked up
+// every time).
 rms_status scratch_ptr(double **out)
 {
     int dev = 0;
@@ -138,11 +176,14 @@ rms_status scratch_ptr(double **out)
     if (e != cudaSuccess) return fail(RMS_E_CUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return fail(RMS_E_INVALID_ARG, "device index beyond the supported range");
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_ptr[dev]) {
+    unsigned long long ctx = current_context_id();
+    if (!g_ptr[dev] || ctx == 0 || ctx != g_ctx[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p) return fail(RMS_E_CUDA, e != cudaSuccess ? cudaGetErrorString(e) : "no address");
+        if (ctx == 0) ctx = current_context_id();  // the lookup may have made the context current
         g_ptr[dev] = (double *)p;
+        g_ctx[dev] = ctx;
     }
     *out = g_ptr[dev];
     return RMS_OK;

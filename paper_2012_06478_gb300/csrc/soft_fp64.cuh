@@ -1,6 +1,6 @@
-// soft_fp64.cuh -- correctly rounded FP64 division, square root and
-// multiplication built on the integer ALU, bit-identical to IEEE 754
-// round-to-nearest-even.
+// soft_fp64.cuh -- correctly rounded FP64 division, square root,
+// multiplication and addition built on the integer ALU, bit-identical to
+// IEEE 754 round-to-nearest-even.
 //
 // Why: GB300's FP64 pipe issues about two operations per clock per SM, a
 // sixty-fourth of its FP32 rate, and an FP64 division or square root is a
@@ -153,10 +153,10 @@ __host__ __device__ __forceinline__ bool div_pos(double a, double b, double &q)
         ++Q;
         R -= (int64_t)B;
     }
-    // round to nearest, ties to even (no ties occur for a quotient)
-    const uint64_t twoR = (uint64_t)R << 1;
-    const uint64_t up = (twoR > B || (twoR == B && (Q & 1ULL))) ? 1ULL : 0ULL;
-    q = double_of(((uint64_t)e << 52) + (Q - kHidden) + up);  // a carry moves into the exponent
+    // round to nearest, ties to even (no ties occur for a quotient): up iff
+    // 2R > B, or 2R == B and Q odd
+    const uint64_t up = ((uint64_t)R << 1) + (Q & 1ULL) > B ? 1ULL : 0ULL;
+    q = double_of((((uint64_t)(e - 1)) << 52) + Q + up);  // Q carries the hidden bit; a carry moves into the exponent
     return true;
 }
 
@@ -172,14 +172,74 @@ __host__ __device__ __forceinline__ bool mul_rn(double a, double b, double &p)
     if ((uint32_t)(ea - 1) >= 0x7FEu || (uint32_t)(eb - 1) >= 0x7FEu) return false;
     const uint64_t A = (ua & kMant) | kHidden, B = (ub & kMant) | kHidden;
     const uint64_t lo = A * B, hi = mulhi(A, B);  // A B in [2^104, 2^106)
-    const uint32_t top = (uint32_t)(hi >> 41);    // 1 when A B >= 2^105
-    const int32_t e = ea + eb - 1023 + (int32_t)top;
+    const bool top = (hi >> 41) != 0ULL;          // A B >= 2^105
+    const int32_t e = ea + eb - 1023 + (top ? 1 : 0);
     if ((uint32_t)(e - 1) >= 0x7FEu) return false;
-    const uint32_t sh = 52u + top;
-    const uint64_t M = (hi << (64u - sh)) | (lo >> sh);  // the top 53 bits
-    const uint64_t rem = lo & ((1ULL << sh) - 1ULL), half = 1ULL << (sh - 1u);
-    const uint64_t up = (rem > half || (rem == half && (M & 1ULL))) ? 1ULL : 0ULL;
-    p = double_of(((ua ^ ub) & 0x8000000000000000ULL) | (((uint64_t)e << 52) + (M - kHidden) + up));
+    // the product brought to [2^105, 2^106) (doubled when below), so that the
+    // 53 kept bits and the 53 below them sit at fixed places
+    const uint64_t hn = top ? hi : (hi << 1) | (lo >> 63);
+    const uint64_t ln = top ? lo : lo << 1;
+    const uint64_t M = (hn << 11) | (ln >> 53);   // in [2^52, 2^53)
+    const uint64_t rem = ln & 0x001FFFFFFFFFFFFFULL;
+    // up iff rem > 2^52, or rem == 2^52 and M odd (ties to even)
+    const uint64_t up = rem + (M & 1ULL) > 0x0010000000000000ULL ? 1ULL : 0ULL;
+    p = double_of(((ua ^ ub) & 0x8000000000000000ULL) | ((((uint64_t)(e - 1)) << 52) + M + up));
+    return true;
+}
+
+// a + b, both finite and normal, of any signs, with a normal nonzero sum
+// (including an overflow to infinity by rounding).  Returns false for a zero,
+// subnormal, infinite or NaN operand, an exact zero sum (whose sign the IEEE
+// rules fix) or a sum out of the normal range.  The larger magnitude's
+// significand sits at bit 62 of a 64-bit word; the smaller one is shifted
+// right by the exponent difference with the bits shifted out folded into a
+// sticky bit, so ten bits below the 53-bit result carry the rounding
+// information through the at most one-bit renormalisation of a sum and the
+// exact renormalisation of a cancelling difference (exponents within one).
+__host__ __device__ __forceinline__ bool add_rn(double a, double b, double &s)
+{
+    uint64_t ua = bits_of(a), ub = bits_of(b);
+    const uint64_t kAbs = 0x7FFFFFFFFFFFFFFFULL;
+    if ((ua & kAbs) < (ub & kAbs)) {  // |a| >= |b| from here on
+        const uint64_t t = ua;
+        ua = ub;
+        ub = t;
+    }
+    const int32_t ea = (int32_t)((ua >> 52) & 0x7FFu), eb = (int32_t)((ub >> 52) & 0x7FFu);
+    if ((uint32_t)(ea - 1) >= 0x7FEu || (uint32_t)(eb - 1) >= 0x7FEu) return false;
+    const uint64_t A = ((ua & kMant) | kHidden) << 10;  // leading one at bit 62
+    const uint64_t Bf = ((ub & kMant) | kHidden) << 10;
+    const uint32_t d = (uint32_t)(ea - eb);
+    uint64_t B;
+    if (d == 0)
+        B = Bf;
+    else if (d < 64)
+        B = (Bf >> d) | ((Bf << (64u - d)) != 0ULL ? 1ULL : 0ULL);
+    else
+        B = 1ULL;  // only a sticky bit is left of b
+    int32_t e = ea;
+    uint64_t S;
+    if (((ua ^ ub) >> 63) == 0) {
+        S = A + B;  // < 2^64
+        if (S >> 63) {
+            S = (S >> 1) | (S & 1ULL);
+            ++e;
+        }
+    } else {
+        S = A - B;
+        if (S == 0ULL) return false;
+#ifdef __CUDA_ARCH__
+        const int32_t lz = __clzll((long long)S) - 1;
+#else
+        const int32_t lz = __builtin_clzll(S) - 1;
+#endif
+        S <<= lz;
+        e -= lz;
+    }
+    if ((uint32_t)(e - 1) >= 0x7FEu) return false;
+    const uint64_t M = S >> 10, r = S & 0x3FFULL;
+    const uint64_t up = (r > 0x200ULL || (r == 0x200ULL && (M & 1ULL))) ? 1ULL : 0ULL;
+    s = double_of((ua & 0x8000000000000000ULL) | (((uint64_t)e << 52) + (M - kHidden) + up));
     return true;
 }
 

@@ -62,6 +62,21 @@ static void check_mul(double a, double b)
     }
 }
 
+static void check_add(double a, double b)
+{
+    double r;
+    if (!add_rn(a, b, r)) {
+        ++g_fallback;
+        return;
+    }
+    ++g_tested;
+    const double x = a + b;
+    if (bits_of(r) != bits_of(x)) {
+        if (g_bad < 10) std::printf("add %a + %a = %a, IEEE %a\n", a, b, r, x);
+        ++g_bad;
+    }
+}
+
 static double make(uint64_t mant, int e) { return double_of(((uint64_t)e << 52) | (mant & kMant)); }
 static double make_s(uint64_t mant, int e, uint64_t sign) { return double_of((sign << 63) | ((uint64_t)e << 52) | (mant & kMant)); }
 
@@ -113,6 +128,31 @@ int main(int argc, char **argv)
         check_mul(make(H, 1023), make(r, 1000));
         check_mul(make(2 * H - 1, 2046), make(H, 1024));   // overflow by rounding or beyond: hardware
         check_mul(make(2 * H - 1, 1), make(H, 1022));      // underflow: hardware
+        // sums and differences: random signs and exponents; exponent gaps of
+        // 0..70 (cancellation, the sticky bit, operands below the last place);
+        // ties (the smaller operand exactly half a unit of the larger); the walk's
+        // ranges (offsets in [0, 1], step components, phases)
+        {
+            const uint64_t sa = g() & 1, sb = g() & 1;
+            check_add(make_s(g(), 1 + (int)(g() % 2046), sa), make_s(g(), 1 + (int)(g() % 2046), sb));
+            const int e0 = 900 + (int)(g() % 200), gap = (int)(g() % 71);
+            check_add(make_s(g(), e0, sa), make_s(g(), e0 - gap, sb));
+            check_add(make_s(g(), e0, sa), make_s(g(), e0 - gap, sa ^ 1));
+            const uint64_t m = g();
+            check_add(make_s(m, e0, sa), make_s(m ^ (g() & 0xFFFF), e0, sa ^ 1));   // heavy cancellation
+            check_add(make_s(m, e0, sa), make_s(0, e0 - 53, sb));                    // half a unit: tie
+            check_add(make_s(m | 1, e0, sa), make_s(0, e0 - 53, sb));
+            check_add(make_s(m, e0, sa), make_s(g() & 1 ? 1 : 0, e0 - 53, sb));
+            check_add(make(g(), 1019 + (int)(g() % 4)), make_s(g(), 1000 + (int)(g() % 22), g() & 1));
+            check_add(make(2 * H - 1, 2046), make(2 * H - 1, 2046));                 // overflow: hardware
+            // a carry out of the top with the bit shifted out by the renormalisation
+            // being the sticky bit: a near-tie that only the sticky bit decides
+            const uint64_t top = (2 * H - 1) & ~(g() & 0xFFFFFF);
+            const int gap2 = 11 + (int)(g() % 50);
+            const uint64_t mb = H | (g() & kMant);
+            check_add(make_s(top, e0, sa), make_s(mb, e0 - gap2, sa));
+            check_add(make_s(top, e0, sa), make_s((mb & ~((1ULL << gap2) - 1)) | ((1ULL << (gap2 - 11)) & kMant), e0 - gap2, sa));
+        }
         // perfect squares and their neighbours
         const uint64_t qq = (H >> 26) | (g() & ((1ULL << 26) - 1));
         const u128 sq = (u128)qq * qq;
@@ -122,7 +162,9 @@ int main(int argc, char **argv)
     // the cases the functions hand back to the hardware
     double t;
     const bool zero_ok = div_pos(0.0, 0.5, t) && bits_of(t) == 0 && !mul_rn(0.0, 1.0, t) && !mul_rn(-1.0, -0.0, t) &&
-                         !mul_rn(INFINITY, 1.0, t) && !mul_rn(0x1p-1040, 2.0, t) && !mul_rn(0x1p-600, 0x1p-500, t);
+                         !mul_rn(INFINITY, 1.0, t) && !mul_rn(0x1p-1040, 2.0, t) && !mul_rn(0x1p-600, 0x1p-500, t) &&
+                         !add_rn(1.0, -1.0, t) && !add_rn(0.0, 1.0, t) && !add_rn(1.0, -0.0, t) &&
+                         !add_rn(0x1p-1022, -0x1.8p-1022, t) && !add_rn(NAN, 1.0, t);
     const bool rejects = !div_pos(-0.0, 0.5, t) && !div_pos(0x1p-1040, 0.5, t) && !div_pos(1.0, 0x1p-1040, t) &&
                          !div_pos(INFINITY, 1.0, t) && !div_pos(1.0, NAN, t) && !div_pos(0x1p-1000, 0x1p+100, t) &&
                          !sqrt_pos(0.0, t) && !sqrt_pos(-1.0, t) && !sqrt_pos(0x1p-1050, t) && !sqrt_pos(INFINITY, t);

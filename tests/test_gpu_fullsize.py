@@ -54,43 +54,65 @@ def _terms(wl, g):
     return al[:, None, None, None] * np.exp(-1j * phi), al
 
 
-def _check_fp32(wl, g64, g32):
-    """|S32 - S64| <= 1e-3 + 4.5 sigma, sigma the standard error of the paired
-    per-walker differences: walkers whose FP32 trajectory has drifted off the
-    FP64 one (rounding drift ~ sqrt(steps)) contribute Monte-Carlo noise that
-    falls as 1/sqrt(W); the 1e-3 bar applies to what is left.  D and K at the
-    last recording time likewise, from the final displacements."""
+def _check_fp32(wl, g64, g32, paired=True):
+    """The FP32 form against the FP64 form on the same walkers: S at every
+    (shape, dir, b), D and K along x, y, z at EVERY recording time.  Bars:
+    |dS| <= 1e-3, |dD| <= 1 % of D, |dK| <= 0.01 max(|K|, 0.1).
+
+    Walkers whose FP32 trajectory drifted off its FP64 twin (the rounding
+    drift grows like sqrt(steps); a face decision flips and the two walkers go
+    separate ways) are still correct samples, but their paired differences
+    are Monte-Carlo noise.  The number of such walkers is part of every
+    message.  paired=True (runs short enough that at most a few per cent of
+    the walkers decorrelate): the flat bars, no allowance.  paired=False
+    (long runs): a bar gets at most itself again as an allowance of 4.5
+    standard errors of the paired per-walker differences (those of the final
+    displacements for D and K, which bound the earlier times': the
+    decorrelated walkers only grow in number), so a run with few walkers
+    cannot pass on its noise; where 4.5 standard errors exceed the bar
+    itself, the comparison has no power and agreement within them is what is
+    asserted; those comparisons are counted and returned."""
+    dec = int(np.any(g32["i"] != g64["i"], axis=1).sum())
+    W = g64["i"].shape[0]
+    if paired:
+        assert dec <= 0.03 * W, f"{dec} of {W} walkers decorrelated: not a paired run"
     dS = np.abs(g32["S"] - g64["S"])
-    if "phase" in g64 and "phase" in g32:
+    sig = np.zeros_like(dS)
+    if dec and not paired:
         e64, a64 = _terms(wl, g64)
         e32, a32 = _terms(wl, g32)
         d = e32 / a32.mean() - e64 / a64.mean()
         sig = np.sqrt(d.real.var(axis=0) + d.imag.var(axis=0)) / np.sqrt(d.shape[0])
-    else:
-        sig = np.zeros_like(dS)
-    assert np.all(dS <= 1e-3 + 4.5 * sig), (dS.max(), sig.max())
     t = wl.rec_steps * wl.dt
-    D64, K64 = _dk(g64["moments"], t)
-    D32, K32 = _dk(g32["moments"], t)
-    if "phase" in g64 and "phase" in g32 and wl.rec_steps[-1] == wl.n_steps:
+    keep = wl.rec_steps <= g64.get("step_end", wl.n_steps)
+    D64, K64 = _dk(g64["moments"][keep], t[keep])
+    D32, K32 = _dk(g32["moments"][keep], t[keep])
+    barD = 0.01 * D64
+    barK = 0.01 * np.maximum(np.abs(K64), 0.1)
+    allowD = np.zeros(3)
+    allowK = np.zeros(3)
+    if dec and not paired:
         x64 = wl.voxel_um * ((g64["i"] - g64["i0"]) + (g64["o"] - g64["o0"]))
         x32 = wl.voxel_um * ((g32["i"] - g32["i0"]) + (g32["o"] - g32["o0"]))
-        W = x64.shape[0]
-        # per-walker weights alpha / <alpha> (D and K are alpha-weighted)
         a64, a32 = np.exp(-g64["A"]), np.exp(-g32["A"])
         w64, w32 = (a64 / a64.mean())[:, None], (a32 / a32.mean())[:, None]
+        te = t[keep][-1]
         m2d = w32 * x32 ** 2 - w64 * x64 ** 2
-        sD = m2d.std(axis=0) / np.sqrt(W) / (2 * t[-1])
-        assert np.all(np.abs(D32[-1] - D64[-1]) <= 0.01 * D64[-1] + 4.5 * sD)
         m4d = w32 * x32 ** 4 - w64 * x64 ** 4
         m2 = (w64 * x64 ** 2).mean(axis=0)
         m4 = (w64 * x64 ** 4).mean(axis=0)
-        sK = np.sqrt((m4d.std(axis=0) / m2 ** 2) ** 2 + (2 * m4 / m2 ** 3 * m2d.std(axis=0)) ** 2)
-        sK = sK / np.sqrt(W)
-        assert np.all(np.abs(K32[-1] - K64[-1]) <= 0.01 * np.maximum(np.abs(K64[-1]), 0.1) + 4.5 * sK)
-    else:
-        assert np.all(np.abs(D32 - D64) <= 0.01 * D64)
-        assert np.all(np.abs(K32 - K64) <= 0.01 * np.maximum(np.abs(K64), 0.1))
+        allowD = 4.5 * m2d.std(axis=0) / np.sqrt(W) / (2 * te)
+        allowK = 4.5 * np.sqrt((m4d.std(axis=0) / m2 ** 2) ** 2 + (2 * m4 / m2 ** 3 * m2d.std(axis=0)) ** 2) / np.sqrt(W)
+    unresolved = 0
+    for name, diff, bar, allow in (("S", dS, np.full_like(dS, 1e-3), 4.5 * sig),
+                                   ("D", np.abs(D32 - D64), barD, np.broadcast_to(allowD, barD.shape)),
+                                   ("K", np.abs(K32 - K64), barK, np.broadcast_to(allowK, barK.shape))):
+        weak = allow > bar
+        unresolved += int(weak.sum())
+        bound = np.where(weak, np.maximum(allow, 2 * bar), bar + allow)
+        msg = f"{name}: worst {np.max(diff / bar):.3g} of its bar; {dec} of {W} walkers decorrelated"
+        assert np.all(diff <= bound), msg
+    return dec, unresolved
 
 
 def test_axons_200x200x400_full(rms):
@@ -100,20 +122,30 @@ def test_axons_200x200x400_full(rms):
     wl = ri.workload("axons-200x200x400")
     g64 = rms.simulate(wl, rms.RMS_FP64, walkers=True)
     _check_sampled(oracle, wl, g64)
-    g32 = rms.simulate(wl, rms.RMS_FP32)
+    g32 = rms.simulate(wl, rms.RMS_FP32, walkers=True)
     _check_fp32(wl, g64, g32)
 
 
 def test_axons_400cubed_t2_ogse(rms):
-    """400^3 axons, unequal D, T2, per-axon kappa, PGSE + five OGSE shapes:
-    every step of the full sequence, 1e4 walkers."""
+    """400^3 axons, unequal D, T2, per-axon kappa, PGSE + five OGSE shapes,
+    2e5 walkers.  The first 2.5e4 steps (walkers still paired): every bar
+    resolved at every recording time.  The whole sequence (2.5e5 steps, where
+    FP32 rounding drift has decorrelated about 14 % of the walkers from their
+    FP64 twins): S and D still within their bars; late K within 4.5 standard
+    errors of the paired differences where those exceed its bar."""
     import oracle
     import rms_inputs as ri
-    wl = ri.workload("axons-400^3-t2-ogse").with_(n_walkers=10_000)
+    wl = ri.workload("axons-400^3-t2-ogse").with_(n_walkers=200_000)
+    k1 = 25_000
+    p64 = rms.simulate(wl, rms.RMS_FP64, walkers=True, step_end=k1)
+    p32 = rms.simulate(wl, rms.RMS_FP32, walkers=True, step_end=k1)
+    p64["step_end"] = k1
+    _check_fp32(wl, p64, p32, paired=True)
     g64 = rms.simulate(wl, rms.RMS_FP64, walkers=True)
     _check_sampled(oracle, wl, g64)
     g32 = rms.simulate(wl, rms.RMS_FP32, walkers=True)
-    _check_fp32(wl, g64, g32)
+    dec, unresolved = _check_fp32(wl, g64, g32, paired=False)
+    assert dec < 0.25 * wl.n_walkers
 
 
 def test_voronoi_512cubed(rms):

@@ -66,9 +66,10 @@ def test_random_substrates_bit_exact(rms, oracle, case, interaction):
 def test_axons_full_with_absorption(rms, oracle):
     """The benchmark workload (200 axons, 1e6 walkers x 1e5 steps) with every
     membrane absorbing (rho = 0.02 um/ms), in the bench launch shape: sampled
-    walkers bit for bit in the plain form; the FP32 form within 1e-3 + 4.5
-    paired standard errors (most walkers saturate, so the paired noise of
-    the drifted walkers is large against the few that remain)."""
+    walkers bit for bit in the plain form; the FP32 form within its bars plus
+    at most the bar again in paired standard errors, with noise-limited
+    comparisons counted (most walkers saturate, so the paired noise of the
+    drifted walkers is large against the few that remain)."""
     import rms_inputs as ri
     from test_gpu_fullsize import _check_fp32
     wl = ri.workload("axons-200x200x400")
@@ -84,7 +85,8 @@ def test_axons_full_with_absorption(rms, oracle):
         for k in ("i", "o", "c", "A", "phase"):
             np.testing.assert_array_equal(g64[k][b:e], o[k].astype(g64[k].dtype), err_msg=k)
     g32 = rms.simulate(wl, rms.RMS_FP32, walkers=True)
-    _check_fp32(wl, g64, g32)
+    dec, _ = _check_fp32(wl, g64, g32, paired=False)
+    assert dec <= 0.05 * W
 
 
 @pytest.mark.parametrize("interaction", [EC, RS])

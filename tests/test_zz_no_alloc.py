@@ -73,6 +73,58 @@ def test_noalloc_readout_matches_regular_readout_twice():
         sub.close()
 
 
+def test_noalloc_at_its_chunk_cap_allocates_nothing():
+    """Many combinations (1 shape x 500 directions x 100 b-values) over 3e5
+    walkers: the scratch holds only 10 walker chunks where rms_run's read-out
+    uses 74, so each chunk covers 30000 walkers.  The result still equals the
+    regular read-out, on two calls in a row, and the second call leaves the
+    device's free memory unchanged (the first may load the library's device
+    code on this device, which takes the scratch array's memory)."""
+    import torch
+    import paper_2012_06478_gb300 as rms
+    from paper_2012_06478_gb300 import _lib
+    rng = np.random.default_rng(23)
+    lab = rng.integers(0, 2, size=(8, 8, 8))
+    n = 40
+    G = np.zeros((1, n))
+    G[0, :10], G[0, 20:30] = 1.0, -1.0
+    wl = make_workload(lab, voxel_um=0.2, D=[2.0, 1.2], kappa=0.3, T2=[60.0, 45.0], dt=2e-3, n_steps=n, G=G,
+                       dirs=rng.normal(size=(500, 3)) / np.sqrt(3), b=np.linspace(0.0, 40.0, 100),
+                       rec_steps=np.array([n]), n_walkers=300_000, seed=23)
+    n_combo = 500 * 100
+    assert (8 * 1024 * 1024 // 8) // (2 * (n_combo + 1)) < -(-wl.n_walkers // 4096)   # the cap binds
+    sub = rms.rms_create_substrate(wl.labels, wl.voxel_um, wl.D, T2=wl.T2, kappa=wl.kappa)
+    seq = rms.rms_set_sequence(sub, wl.dt, wl.G, wl.dirs, wl.b, wl.rec_steps)
+    run = rms.rms_run(seq, wl.n_walkers, wl.seed, rms.RMS_FP64)
+    S_ref, _, asum_ref = rms.rms_read_signal(run)
+    st = rms.rms_read_walkers(run)
+    bs = rms.rms_sequence_bvalues(seq)
+    for call in range(2):
+        rc, S, asum = _noalloc(torch, _lib.lib, st, bs, wl)
+        assert rc == _lib.RMS_OK, _lib.last_error()
+        err = np.abs(S - S_ref) / np.maximum(np.abs(S_ref), 1e-3)
+        assert err.max() <= 1e-12, (call, err.max())
+        assert abs(asum - asum_ref) <= 1e-12 * asum_ref
+    run.close()
+    seq.close()
+    sub.close()
+    # the second call took no device memory: measured around a third call with
+    # its inputs and outputs already in place
+    phase = torch.from_numpy(np.ascontiguousarray(st["phase"])).cuda()
+    A = torch.from_numpy(st["A"]).cuda()
+    b_s, dirs, b = (torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (bs, wl.dirs, wl.b))
+    re = torch.zeros(n_combo, dtype=torch.float64, device="cuda")
+    im = torch.zeros_like(re)
+    torch.cuda.synchronize()
+    before = torch.cuda.mem_get_info()[0]
+    rc = _lib.lib.rms_readout_noalloc(phase.data_ptr(), A.data_ptr(), wl.n_walkers, 1, b_s.data_ptr(), 500,
+                                      dirs.data_ptr(), 100, b.data_ptr(), re.data_ptr(), im.data_ptr(), None,
+                                      C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert rc == _lib.RMS_OK
+    assert torch.cuda.mem_get_info()[0] == before
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     import torch
     from paper_2012_06478_gb300 import _lib
