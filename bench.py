@@ -491,7 +491,7 @@ def kernel_source_sha(form):
     one form, to tell whether a profile summary still describes it."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2012_06478_gb300", "csrc")
-    files = [os.path.join(csrc, f) for f in ("walk_kernel.cuh", "rms_device.cuh", f"walk_{form}.cu")]
+    files = [os.path.join(csrc, f) for f in ("walk_kernel.cuh", "rms_device.cuh", "soft_fp64.cuh", f"walk_{form}.cu")]
     files.append(os.path.join(ROOT, "paper_2012_06478_gb300", "build.py"))
     h = hashlib.sha256()
     for f in files:

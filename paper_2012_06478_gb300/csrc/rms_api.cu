@@ -887,7 +887,7 @@ ReqDesc<Real> rms::run_desc(rms_run_handle *r)
     rms_substrate *sub = q->sub;
     ReqDesc<Real> d{};
     d.g = Geometry{sub->d_labels, sub->nx, sub->ny, sub->nz, sub->periodic[0], sub->periodic[1], sub->periodic[2],
-                   sub->voxel_um};
+                   sub->voxel_um, (float)sub->voxel_um};
     if constexpr (std::is_same<Real, float>::value) {
         d.t = Tables<float>{q->d_s32, q->d_dtR32, q->d_T, q->d_Tmt, sub->L, q->d_wG32, q->d_flags, q->d_rec_of,
                             q->d_mode, q->any_relax, q->d_trig};

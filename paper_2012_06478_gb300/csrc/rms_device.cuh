@@ -118,6 +118,7 @@ struct Geometry {
     int32_t nx, ny, nz;
     int32_t per_x, per_y, per_z;
     double voxel_um;
+    float voxel_f;  // voxel_um rounded to single precision (the FP32 form's phase)
 };
 
 template <typename Real>

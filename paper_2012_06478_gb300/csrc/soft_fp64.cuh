@@ -1,6 +1,6 @@
-// soft_fp64.cuh -- correctly rounded FP64 division, square root,
-// multiplication and addition built on the integer ALU, bit-identical to
-// IEEE 754 round-to-nearest-even.
+// soft_fp64.cuh -- correctly rounded FP64 division, square root and
+// multiplication built on the integer ALU, bit-identical to IEEE 754
+// round-to-nearest-even.
 //
 // Why: GB300's FP64 pipe issues about two operations per clock per SM, a
 // sixty-fourth of its FP32 rate, and an FP64 division or square root is a
@@ -160,11 +160,26 @@ __host__ __device__ __forceinline__ bool div_pos(double a, double b, double &q)
     return true;
 }
 
+// The product of the significands of a and b rounded to 53 bits, given the
+// biased exponent e of the result: the 106-bit product is exact in two words,
+// brought to [2^105, 2^106) (doubled when below), so that the 53 kept bits
+// and the 53 below them sit at fixed places; rounding is to nearest with ties
+// to even (products do have ties).
+__host__ __device__ __forceinline__ double mul_core(uint64_t ua, uint64_t ub, uint64_t lo, uint64_t hi, bool top,
+                                                    int32_t e)
+{
+    const uint64_t hn = top ? hi : (hi << 1) | (lo >> 63);
+    const uint64_t ln = top ? lo : lo << 1;
+    const uint64_t M = (hn << 11) | (ln >> 53);  // in [2^52, 2^53)
+    const uint64_t rem = ln & 0x001FFFFFFFFFFFFFULL;
+    // up iff rem > 2^52, or rem == 2^52 and M odd
+    const uint64_t up = rem + (M & 1ULL) > 0x0010000000000000ULL ? 1ULL : 0ULL;
+    return double_of(((ua ^ ub) & 0x8000000000000000ULL) | ((((uint64_t)(e - 1)) << 52) + M + up));
+}
+
 // a * b, both finite, normal and of any sign, with a normal product
 // (including an overflow to infinity by rounding).  Returns false for a zero,
 // subnormal, infinite or NaN operand, or a product out of the normal range.
-// The 106-bit product of the significands is exact in two words; rounding to
-// 53 bits is to nearest with ties to even (products do have ties).
 __host__ __device__ __forceinline__ bool mul_rn(double a, double b, double &p)
 {
     const uint64_t ua = bits_of(a), ub = bits_of(b);
@@ -175,80 +190,27 @@ __host__ __device__ __forceinline__ bool mul_rn(double a, double b, double &p)
     const bool top = (hi >> 41) != 0ULL;          // A B >= 2^105
     const int32_t e = ea + eb - 1023 + (top ? 1 : 0);
     if ((uint32_t)(e - 1) >= 0x7FEu) return false;
-    // the product brought to [2^105, 2^106) (doubled when below), so that the
-    // 53 kept bits and the 53 below them sit at fixed places
-    const uint64_t hn = top ? hi : (hi << 1) | (lo >> 63);
-    const uint64_t ln = top ? lo : lo << 1;
-    const uint64_t M = (hn << 11) | (ln >> 53);   // in [2^52, 2^53)
-    const uint64_t rem = ln & 0x001FFFFFFFFFFFFFULL;
-    // up iff rem > 2^52, or rem == 2^52 and M odd (ties to even)
-    const uint64_t up = rem + (M & 1ULL) > 0x0010000000000000ULL ? 1ULL : 0ULL;
-    p = double_of(((ua ^ ub) & 0x8000000000000000ULL) | ((((uint64_t)(e - 1)) << 52) + M + up));
+    p = mul_core(ua, ub, lo, hi, top, e);
     return true;
 }
 
-// a + b, both finite and normal, of any signs, with a normal nonzero sum
-// (including an overflow to infinity by rounding).  Returns false for a zero,
-// subnormal, infinite or NaN operand, an exact zero sum (whose sign the IEEE
-// rules fix) or a sum out of the normal range.  The larger magnitude's
-// significand sits at bit 62 of a 64-bit word; the smaller one is shifted
-// right by the exponent difference with the bits shifted out folded into a
-// sticky bit, so ten bits below the 53-bit result carry the rounding
-// information through the at most one-bit renormalisation of a sum and the
-// exact renormalisation of a cancelling difference (exponents within one).
-__host__ __device__ __forceinline__ bool add_rn(double a, double b, double &s)
+// a * b for operands that are known to be normal, with a product known to be
+// normal (the caller's ranges guarantee it): mul_rn without its checks.
+__host__ __device__ __forceinline__ double mul_normal(double a, double b)
 {
-    uint64_t ua = bits_of(a), ub = bits_of(b);
-    const uint64_t kAbs = 0x7FFFFFFFFFFFFFFFULL;
-    if ((ua & kAbs) < (ub & kAbs)) {  // |a| >= |b| from here on
-        const uint64_t t = ua;
-        ua = ub;
-        ub = t;
-    }
+    const uint64_t ua = bits_of(a), ub = bits_of(b);
     const int32_t ea = (int32_t)((ua >> 52) & 0x7FFu), eb = (int32_t)((ub >> 52) & 0x7FFu);
-    if ((uint32_t)(ea - 1) >= 0x7FEu || (uint32_t)(eb - 1) >= 0x7FEu) return false;
-    const uint64_t A = ((ua & kMant) | kHidden) << 10;  // leading one at bit 62
-    const uint64_t Bf = ((ub & kMant) | kHidden) << 10;
-    const uint32_t d = (uint32_t)(ea - eb);
-    uint64_t B;
-    if (d == 0)
-        B = Bf;
-    else if (d < 64)
-        B = (Bf >> d) | ((Bf << (64u - d)) != 0ULL ? 1ULL : 0ULL);
-    else
-        B = 1ULL;  // only a sticky bit is left of b
-    int32_t e = ea;
-    uint64_t S;
-    if (((ua ^ ub) >> 63) == 0) {
-        S = A + B;  // < 2^64
-        if (S >> 63) {
-            S = (S >> 1) | (S & 1ULL);
-            ++e;
-        }
-    } else {
-        S = A - B;
-        if (S == 0ULL) return false;
-#ifdef __CUDA_ARCH__
-        const int32_t lz = __clzll((long long)S) - 1;
-#else
-        const int32_t lz = __builtin_clzll(S) - 1;
-#endif
-        S <<= lz;
-        e -= lz;
-    }
-    if ((uint32_t)(e - 1) >= 0x7FEu) return false;
-    const uint64_t M = S >> 10, r = S & 0x3FFULL;
-    const uint64_t up = (r > 0x200ULL || (r == 0x200ULL && (M & 1ULL))) ? 1ULL : 0ULL;
-    s = double_of((ua & 0x8000000000000000ULL) | (((uint64_t)e << 52) + (M - kHidden) + up));
-    return true;
+    const uint64_t A = (ua & kMant) | kHidden, B = (ub & kMant) | kHidden;
+    const uint64_t lo = A * B, hi = mulhi(A, B);
+    const bool top = (hi >> 41) != 0ULL;
+    return mul_core(ua, ub, lo, hi, top, ea + eb - 1023 + (top ? 1 : 0));
 }
 
-// sqrt(x) for a normal x > 0.  Returns false otherwise.
-__host__ __device__ __forceinline__ bool sqrt_pos(double x, double &r)
+// sqrt(x) for an x known to be normal and positive (no checks).
+__host__ __device__ __forceinline__ double sqrt_normal(double x)
 {
     const uint64_t ux = bits_of(x);
     const int32_t ex = (int32_t)(ux >> 52);
-    if ((uint32_t)(ex - 1) >= 0x7FEu) return false;  // zero, subnormal, negative, inf, NaN
     const uint64_t M = (ux & kMant) | kHidden;
     const int32_t E = ex - 1023;                        // x = M 2^(E - 52)
     const bool odd = (E & 1) != 0;
@@ -291,7 +253,16 @@ __host__ __device__ __forceinline__ bool sqrt_pos(double x, double &r)
     // round to nearest: sqrt(X) >= q + 1/2 iff X - q^2 > q (no ties)
     const uint64_t up = (uint64_t)R > q ? 1ULL : 0ULL;
     const int32_t er = ((E - (odd ? 1 : 0)) >> 1) + 1023;
-    r = double_of(((uint64_t)er << 52) + (q - kHidden) + up);
+    return double_of((((uint64_t)(er - 1)) << 52) + q + up);
+}
+
+// sqrt(x) for a normal x > 0.  Returns false otherwise (zero, subnormal,
+// negative, infinite or NaN x).
+__host__ __device__ __forceinline__ bool sqrt_pos(double x, double &r)
+{
+    const int32_t ex = (int32_t)(bits_of(x) >> 52);
+    if ((uint32_t)(ex - 1) >= 0x7FEu) return false;
+    r = sqrt_normal(x);
     return true;
 }
 

@@ -90,10 +90,9 @@ __device__ __forceinline__ void octant_map(uint32_t oct, double cs, double sn, d
 // inlined, a predicated copy would run on the FP64 pipe at every call.
 static __device__ __noinline__ double hw_mul(double a, double b) { return a * b; }
 static __device__ __noinline__ double hw_div(double a, double b) { return a / b; }
-static __device__ __noinline__ double hw_sqrt(double x) { return sqrt(x); }
 
-// FP64 products, quotients of non-negative operands and square roots on the
-// integer ALU (sfp::mul_rn, div_pos, sqrt_pos: the IEEE results bit for bit).
+// FP64 products and quotients of non-negative operands on the integer ALU
+// (sfp::mul_rn, div_pos: the IEEE results bit for bit).
 // mulr is the product of the form: this one for FP64, a plain multiply for FP32.
 __device__ __forceinline__ double dmul(double a, double b)
 {
@@ -107,12 +106,7 @@ __device__ __forceinline__ double ddiv_nn(double a, double b)
     if (!sfp::div_pos(a, b, q)) q = hw_div(a, b);
     return q;
 }
-__device__ __forceinline__ double dsqrt(double x)
-{
-    double r;
-    if (!sfp::sqrt_pos(x, r)) r = hw_sqrt(x);
-    return r;
-}
+
 __device__ __forceinline__ double mulr(double a, double b) { return dmul(a, b); }
 __device__ __forceinline__ float mulr(float a, float b) { return a * b; }
 
@@ -159,7 +153,14 @@ __device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, const d
     const bool zneg = x0 >= 0x80000000u;
     const uint32_t kmag = zneg ? 2u * x0 + 1u : 0xFFFFFFFFu - 2u * x0;  // |k|
     const double z = odd_scaled(kmag, zneg, -32);
-    const double r = dsqrt(u64_scaled_rn(0ULL - (unsigned long long)kmag * kmag));  // argument in (2^-32, 1]
+    // Every value below is normal and nonzero for every pair of words, so the
+    // integer-ALU products and square root need neither range checks nor a
+    // hardware fallback: the argument of the root is at least (2^33 - 1) 2^-64;
+    // |e| lies in [2^-30, 2^-11] pi/4, t = e^2 in [2^-61, 2^-22], the table's
+    // cosines and sines in [3.8e-4, 1], cs and sn in [7e-10, 1] (the angle is at
+    // least 2^-30 pi/4), r in [2^-16, 1]; every product stays far inside the
+    // normal range.
+    const double r = sfp::sqrt_normal(u64_scaled_rn(0ULL - (unsigned long long)kmag * kmag));
     const uint32_t oct = x1 >> 29;
     uint32_t m = x1 & 0x1FFFFFFFu;
     if (oct & 1u) m = 0x1FFFFFFFu - m;
@@ -168,17 +169,18 @@ __device__ __forceinline__ void direction_from(uint32_t x0, uint32_t x1, const d
     const uint32_t j = m >> 19;
     const int32_t lo = (int32_t)(m & 0x7FFFFu);
     const int32_t e_int = 2 * lo + 1 - (1 << 19);  // odd
-    const double e = dmul(odd_scaled((uint32_t)(e_int < 0 ? -e_int : e_int), e_int < 0, -30), 0.78539816339744830962);
-    const double t = dmul(e, e);
-    const double se = e + dmul(dmul(e, t), -1.0 / 6.0 + dmul(t, 1.0 / 120.0));
-    const double ce = 1.0 + dmul(t, -1.0 / 2.0 + dmul(t, 1.0 / 24.0));
+    using sfp::mul_normal;
+    const double e = mul_normal(odd_scaled((uint32_t)(e_int < 0 ? -e_int : e_int), e_int < 0, -30), 0.78539816339744830962);
+    const double t = mul_normal(e, e);
+    const double se = e + mul_normal(mul_normal(e, t), -1.0 / 6.0 + mul_normal(t, 1.0 / 120.0));
+    const double ce = 1.0 + mul_normal(t, -1.0 / 2.0 + mul_normal(t, 1.0 / 24.0));
     const double cj = __ldg(trig + 2 * j), sj = __ldg(trig + 2 * j + 1);
-    const double cs = dmul(cj, ce) - dmul(sj, se);
-    const double sn = dmul(sj, ce) + dmul(cj, se);
+    const double cs = mul_normal(cj, ce) - mul_normal(sj, se);
+    const double sn = mul_normal(sj, ce) + mul_normal(cj, se);
     double cx, sy;
     octant_map(oct, cs, sn, cx, sy);
-    n[0] = dmul(r, cx);
-    n[1] = dmul(r, sy);
+    n[0] = mul_normal(r, cx);
+    n[1] = mul_normal(r, sy);
     n[2] = z;
 }
 
@@ -301,7 +303,13 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
     const int32_t stride[3] = {1, g.nx, g.nx * g.ny};
     const int32_t per[3] = {g.per_x, g.per_y, g.per_z};
     const int32_t L = t.n_labels;
-    const Real lp = (Real)g.voxel_um;  // voxel edge in the form's precision, converted once
+    // voxel edge in the form's precision (the single-precision value comes from
+    // the host: a conversion here would run on the FP64 pipe at every step)
+    Real lp;
+    if constexpr (kF64)
+        lp = g.voxel_um;
+    else
+        lp = g.voxel_f;
 
     Real o[3], o0[3];
     int32_t di[3], wc[3];
@@ -500,7 +508,11 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
                     T[a] = (dgt0(d[a]) || dlt0(d[a])) ? ddiv_nn(num, den) : kInf;
                 }
                 double tau = 0.0;
-#pragma unroll  // unrolled: each event index is a constant (measured 5 % faster, FP32)
+                // not unrolled in the plain form: its event pass carries the integer-ALU
+                // arithmetic (and the rare re-timing after a change of step length, with
+                // three divisions); three copies of it measured 7 % slower, from
+                // instruction fetch
+#pragma unroll 1
                 for (int ev = 0; ev < 3; ++ev) {
                     int best = 0;
                     double tmin = T[0];

@@ -1,11 +1,11 @@
-"""The plain FP64 form's divisions and square root run on the integer ALU
-(paper_2012_06478_gb300/csrc/soft_fp64.cuh); they must give the IEEE
-round-to-nearest-even result bit for bit.  The same source, compiled for the
-host, is compared with the host's IEEE division and sqrt over every normal
+"""The plain FP64 form's products, divisions and square root run on the
+integer ALU (paper_2012_06478_gb300/csrc/soft_fp64.cuh); they must give the
+IEEE round-to-nearest-even result bit for bit.  The same source, compiled for
+the host, is compared with the host's IEEE operations over every normal
 exponent, the walker step's operand ranges, values within one unit of a
-rounding midpoint, powers of two and extreme mantissas, and perfect squares;
-the operands it hands back to the hardware are checked to be exactly the
-ones outside its range."""
+rounding midpoint (products with exact ties), powers of two and extreme
+mantissas, and perfect squares; the operands it hands back to the hardware
+are checked to be exactly the ones outside its range."""
 import os
 import subprocess
 
