@@ -13,6 +13,13 @@ x 11 b-values.
 Prints one JSON line (rank 0).  Under torchrun every rank runs its own 1e6
 walkers (distinct global walker ids): weak scaling, no collective on the data
 path; the per-rank sums are combined after the timed region.
+
+Before the timed region the run measures the machine peaks its rooflines
+divide by (random 2-byte gathers from a volume of the label volume's size,
+FP64 adds and multiplies; include/rms_peaks.h).  After it: the FP32 form
+against the plain FP64 form at every recording time, the same metric end to
+end through the C ABI from host buffers, the serving stream under both tick
+policies and in the FP64 form, and the oracle on a walker sample on the host.
 """
 from __future__ import annotations
 

@@ -29,7 +29,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rms_oracle.c")
-_LIB = os.path.join(_HERE, "librms_oracle.so")
+# RMS_ORACLE_SANITIZE=1: a separate build under AddressSanitizer and
+# UndefinedBehaviorSanitizer (the process must preload the ASan runtime)
+_SANITIZE = os.environ.get("RMS_ORACLE_SANITIZE") == "1"
+_LIB = os.path.join(_HERE, "librms_oracle_san.so" if _SANITIZE else "librms_oracle.so")
 _lib = None
 
 MOMENT_NAMES = (["1"] + [a + b for i, a in enumerate("xyz") for b in "xyz"[i:]] +
@@ -42,7 +45,9 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, no fast math)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math",
+        san = (["-fsanitize=address,undefined", "-fno-sanitize-recover=all", "-fno-omit-frame-pointer", "-g"]
+               if _SANITIZE else [])
+        subprocess.check_call(["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", *san,
                                "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB

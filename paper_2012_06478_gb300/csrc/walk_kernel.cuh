@@ -753,14 +753,15 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
     }
 }
 
-// Resident blocks per SM the register allocation must allow, for the
-// one-shape kernels (0: no bound, the compiler's choice).  The plain form's
-// integer-ALU arithmetic is made of long dependent chains, whose latency more
-// warps hide: 5 blocks (at most 102 registers) measured 6 % faster than the
-// unconstrained 4.  The FP32 form keeps its 7; kernels with more shapes keep
-// the registers their phases need.
+// Resident blocks per SM the register allocation must allow (0: no bound,
+// the compiler's choice).  The plain form's one-shape kernel: its integer-ALU
+// arithmetic is made of long dependent chains, whose latency more warps hide,
+// and 5 blocks (at most 102 registers) measured 6 % faster than the
+// unconstrained 4.  The FP32 form is left to the compiler (it settles on 7
+// blocks; a bound of 7, 8 or 9 measured no faster); kernels with more shapes
+// keep the registers their phases need.
 template <typename Real, int NS>
-constexpr int kWalkMinBlocks = NS == 1 ? (std::is_same<Real, double>::value ? 5 : 7) : 0;
+constexpr int kWalkMinBlocks = (NS == 1 && std::is_same<Real, double>::value) ? 5 : 0;
 
 // One run: block b of the grid advances walkers b*kWalkBlock ... of the run.
 template <typename Real, int NS, bool HASH, int IM, bool MT>
