@@ -287,17 +287,21 @@ rms_status tick_once(rms_server *s)
             if (q->precision == prec && bucket_index(q->bucket) == g % 4) blocks += q->run->n_blocks;
         const int64_t slots = s->slots[g / 4][g % 4];
         const int64_t waves = std::min<int64_t>(64, std::max<int64_t>(1, blocks / std::max<int64_t>(slots, 1)));
-        for (size_t i = 0; i < s->active.size(); ++i) {
-            Request *q = s->active[i];
-            if (q->precision != prec || bucket_index(q->bucket) != g % 4) continue;
-            int64_t quota = s->cfg.steps_per_tick;
-            if (s->cfg.policy == RMS_SERVE_FILL && q->run->n_blocks < slots) quota *= waves;
-            const int64_t k0 = q->progress;
-            const int64_t k1 = std::min<int64_t>(q->seq->n_steps, k0 + quota);
-            range[i] = {k0, k1};
-            ++q->ticks;
-            for (int64_t b = 0; b < q->run->n_blocks; ++b) T[off++] = BlockTask{q->slot, 0, b, k0, k1};
-        }
+        // the requests that run the whole launch go first, so that their blocks
+        // take slots from the start instead of stretching its end
+        for (int pass = 0; pass < 2; ++pass)
+            for (size_t i = 0; i < s->active.size(); ++i) {
+                Request *q = s->active[i];
+                if (q->precision != prec || bucket_index(q->bucket) != g % 4) continue;
+                const bool filling = s->cfg.policy == RMS_SERVE_FILL && q->run->n_blocks < slots && waves > 1;
+                if (filling != (pass == 0)) continue;
+                const int64_t quota = s->cfg.steps_per_tick * (filling ? waves : 1);
+                const int64_t k0 = q->progress;
+                const int64_t k1 = std::min<int64_t>(q->seq->n_steps, k0 + quota);
+                range[i] = {k0, k1};
+                ++q->ticks;
+                for (int64_t b = 0; b < q->run->n_blocks; ++b) T[off++] = BlockTask{q->slot, 0, b, k0, k1};
+            }
         count[g] = off - start[g];
     }
     cudaGraph_t graph = nullptr;
