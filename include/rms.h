@@ -403,9 +403,9 @@ rms_status rms_philox4x32_10(const uint32_t *ctr, const uint32_t *key, int64_t n
 /* ------------------------------------------------------------------ */
 #define RMS_NOALLOC_SCRATCH_BYTES (8 * 1024 * 1024)
 
-/* The same read-out as rms_run's (Eq. 7: S = sum alpha e^{-i phi} / sum
- * alpha, phi = q g.Phi_s, q = sqrt(b / b_s), alpha = exp(-A)) over walker data
- * the caller holds.  Every pointer is a DEVICE pointer of the current device:
+/* The same read-out as rms_run's (S = sum alpha e^{-i phi} / sum alpha,
+ * phi = q g.Phi_s, q = sqrt(b / b_s), alpha = exp(-A)) over walker data the
+ * caller holds.  Every pointer is a DEVICE pointer of the current device:
  *   phase     : n_walkers*n_shapes*3 doubles, row-major (walker, shape, axis),
  *               the layout rms_read_walkers returns
  *   A         : n_walkers doubles, exponent of Eq. 5

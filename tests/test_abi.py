@@ -129,3 +129,21 @@ def test_product_code_never_reaches_the_oracle():
                 if fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                     text = open(os.path.join(dirpath, fn), encoding="utf-8").read()
                     assert not pat.search(text), os.path.join(dirpath, fn)
+
+
+def test_normalise_partials_on_the_host():
+    """rms_normalise_partials is host arithmetic (no device): S = num / sum
+    alpha element by element, the division rms_read_signal applies; bad
+    sizes and null arrays are refused."""
+    import numpy as np
+    from paper_2012_06478_gb300 import _lib
+    import paper_2012_06478_gb300 as rms
+    rng = np.random.default_rng(5)
+    num = rng.normal(size=(2, 3, 4)) + 1j * rng.normal(size=(2, 3, 4))
+    S = rms.rms_normalise_partials(num, 7.25)
+    np.testing.assert_array_equal(S.real, num.real / 7.25)
+    np.testing.assert_array_equal(S.imag, num.imag / 7.25)
+    assert S.shape == num.shape
+    assert _lib.lib.rms_normalise_partials(-1, None, None, 1.0, None, None) == _lib.RMS_E_INVALID_ARG
+    assert _lib.lib.rms_normalise_partials(3, None, None, 1.0, None, None) == _lib.RMS_E_INVALID_ARG
+    assert _lib.lib.rms_normalise_partials(0, None, None, 1.0, None, None) == _lib.RMS_OK
