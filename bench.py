@@ -201,7 +201,7 @@ def ncu_case(args):
     n = args.ncu_case
     wl = wl.with_(n_steps=n, G=np.asarray(wl.G)[:, :n], rec_steps=wl.rec_steps[wl.rec_steps <= n])
     for prec in (rms.RMS_FP32, rms.RMS_FP64):
-        r = rms.simulate(wl, prec, steps_per_launch=n)
+        r = rms.simulate(wl, prec, steps_per_launch=n, morton=args.morton)
         print(f"precision {prec}: {wl.n_walkers} walkers x {n} steps, walk {r['step_ms']:.2f} ms", flush=True)
 
 
@@ -269,6 +269,10 @@ def main():
     ap.add_argument("--serving-fp64-requests", type=int, default=64,
                     help="requests of the stream also served in the FP64 plain form (0: none)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--steps-per-launch", type=int, default=0,
+                    help="steps per walk launch (0: the library's default, about 2e9 walker-steps per launch)")
+    ap.add_argument("--morton", action="store_true",
+                    help="re-bucket walkers in Morton order of their voxel before every launch (RMS_MORTON)")
     ap.add_argument("--ncu-case", type=int, default=0,
                     help="profiling case: one FP32 and one FP64 run of the workload with this many steps "
                          "(one walk launch each), no timing output")
@@ -299,6 +303,7 @@ def main():
     w_begin, _ = shard.shard_range(rank, world, W, weak=True)
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
+    run_flags = rms.RMS_MORTON if args.morton else 0
 
     sub = rms.rms_create_substrate(wl.labels, wl.voxel_um, wl.D, T2=wl.T2, T1=wl.T1, kappa=wl.kappa,
                                    dead=wl.dead, periodic=wl.periodic, stream=sp, rho=wl.rho, conc=wl.conc,
@@ -324,7 +329,8 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            run = rms.rms_run(seq, W, wl.seed, precision, 0, w_begin, 0, sp, wl.interaction)
+            run = rms.rms_run(seq, W, wl.seed, precision, run_flags, w_begin, args.steps_per_launch, sp,
+                              wl.interaction)
             e1.record(stream)
             res = rms.rms_read_signal(run)
             if it >= n_warm:
@@ -368,9 +374,11 @@ def main():
         v = shard.allreduce_partials(shard.pack_partials(num32, res32[2], res32[1]))
         shard.unpack_partials(v, res32[0].shape, res32[1].shape)
 
-    spl = max(64, min(2_000_000_000 // W, wl.n_steps))
+    spl = args.steps_per_launch or max(64, min(2_000_000_000 // W, wl.n_steps))
     n_walk = math.ceil(wl.n_steps / spl)
     launches_per_step = 1 + n_walk + (1 if wl.rec_steps.size else 0) + 3
+    if args.morton:  # per walk launch: the key, 5 kernels per radix pass, the permutation
+        launches_per_step += n_walk * (2 + 5 * morton_passes(wl.shape_xyz))
     sm_mhz = clk.summary().get("sm_mhz") or pk.get("sm_max_mhz") or 2070.0
     kernel = f"walk_kernel<{{}},1,false,{INTERACTIONS[args.interaction]},{'true' if args.rho > 0 else 'false'}>"
     variant = args.interaction == "ec" and args.rho == 0
@@ -386,6 +394,8 @@ def main():
                    "grid_xyz": list(wl.shape_xyz), "voxel_um": wl.voxel_um, "labels": wl.n_labels,
                    "n_dirs": int(wl.dirs.shape[0]), "n_b": int(wl.b.size), "n_rec": int(wl.rec_steps.size),
                    "interaction": args.interaction, "rho_um_per_ms": args.rho,
+                   "walker_order": "Morton order of the voxel, re-bucketed before every launch" if args.morton
+                   else "walker id",
                    "precision": "fp32 form (headline); fp64 plain form in fp64_plain",
                    "l2": "flushed between timed iterations (256 MiB write)", "parallelism": f"walker shards x{world}"},
         "fp64_plain": {"value": value64, "unit": UNIT, "dtype": "f64", "steps": args.fp64_steps, "warmup": args.fp64_warmup,
@@ -398,6 +408,7 @@ def main():
         "peaks": live,
         "clocks": clk.summary(),
     }
+    line["config"]["steps_per_launch"] = spl
     if not args.no_e2e:
         line["e2e"] = e2e(rms, torch, wl, W, w_begin, sp, args, world, max_over_ranks)
     if not args.no_serving and world == 1 and variant:
@@ -736,6 +747,13 @@ def paired_sigma(torch, wl, b_s, w64, w32, dev="cuda"):
     return (var.clamp_min(0) / W).sqrt().cpu().numpy()
 
 
+def morton_passes(shape_xyz):
+    """Radix passes of RMS_MORTON's sort for a volume (8 key bits per pass;
+    3 bits per coordinate bit, coordinates shifted to at most 8 bits)."""
+    bits = int(max(shape_xyz) - 1).bit_length()
+    return (3 * min(bits, 8) + 7) // 8
+
+
 def e2e(rms, torch, wl, W, w_begin, sp, args, world, max_over_ranks):
     """The same metric through the C ABI from host buffers: upload of the
     label volume and tables, the run, the read-back of the signal and moments."""
@@ -752,7 +770,8 @@ def e2e(rms, torch, wl, W, w_begin, sp, args, world, max_over_ranks):
                                        periodic=wl.periodic, stream=sp, rho=wl.rho, conc=wl.conc, lam=wl.lam,
                                        perm_model=wl.perm_model)
         seq = rms.rms_set_sequence(sub, wl.dt, wl.G, wl.dirs, wl.b, wl.rec_steps, mode=wl.mode)
-        run = rms.rms_run(seq, W, wl.seed, rms.RMS_FP32, 0, w_begin, 0, sp, wl.interaction)
+        run = rms.rms_run(seq, W, wl.seed, rms.RMS_FP32, rms.RMS_MORTON if args.morton else 0, w_begin,
+                          args.steps_per_launch, sp, wl.interaction)
         rms.rms_read_signal(run)
         el = time.perf_counter() - t0
         run.close()

@@ -27,6 +27,7 @@ RMS_FP32 = 1
 RMS_TRAJ_HASH = 1
 RMS_CHECKED = 2
 RMS_COUNTS = 4
+RMS_MORTON = 8
 RMS_EC = 0
 RMS_RS = 1
 RMS_ERL = 2
@@ -94,6 +95,7 @@ SIGNATURES = {
                       C.c_int),
     "rms_run_query": ([C.c_void_p], C.c_int),
     "rms_read_counts": ([C.c_void_p, C.c_void_p], C.c_int),
+    "rms_read_slots": ([C.c_void_p, C.c_void_p], C.c_int),
     "rms_cancel": ([C.c_void_p], C.c_int),
     "rms_read_signal": ([C.c_void_p] + [C.c_void_p] * 4, C.c_int),
     "rms_read_walkers": ([C.c_void_p] + [C.c_void_p] * 8, C.c_int),

@@ -17,14 +17,14 @@ from typing import Optional, Sequence as Seq
 import numpy as np
 
 from . import _lib as L
-from ._lib import (RMS_CHECKED, RMS_COUNTS, RMS_EC, RMS_ERL, RMS_FP32, RMS_FP64, RMS_PEAK_FP64_ADD, RMS_PEAK_FP64_FMA,
+from ._lib import (RMS_CHECKED, RMS_COUNTS, RMS_EC, RMS_MORTON, RMS_ERL, RMS_FP32, RMS_FP64, RMS_PEAK_FP64_ADD, RMS_PEAK_FP64_FMA,
                    RMS_PEAK_FP64_MUL, RMS_PEAK_GATHER, RMS_PEAK_GATHER_DEP, RMS_RS, RMS_SERVE_FILL, RMS_SERVE_STEPS,
                    RMS_TRAJ_HASH, RmsError, check)
 
 __all__ = ["rms_create_substrate", "rms_set_sequence", "rms_run", "rms_read_signal", "rms_read_walkers",
-           "rms_read_counts", "rms_cancel", "rms_run_query", "rms_destroy_run", "rms_destroy_sequence",
+           "rms_read_counts", "rms_read_slots", "rms_cancel", "rms_run_query", "rms_destroy_run", "rms_destroy_sequence",
            "rms_destroy_substrate", "rms_sequence_bvalues", "rms_run_step_time_ms", "simulate", "current_stream",
-           "RMS_FP32", "RMS_FP64", "RMS_TRAJ_HASH", "RMS_CHECKED", "RMS_COUNTS", "RMS_EC", "RMS_RS", "RMS_ERL",
+           "RMS_FP32", "RMS_FP64", "RMS_TRAJ_HASH", "RMS_CHECKED", "RMS_COUNTS", "RMS_MORTON", "RMS_EC", "RMS_RS", "RMS_ERL",
            "RmsError", "MOMENT_NAMES", "Server", "rms_measure_peak", "rms_device_sm_count", "rms_read_partials",
            "rms_normalise_partials", "rms_philox4x32_10", "RMS_PEAK_FP64_ADD", "RMS_PEAK_FP64_MUL", "RMS_PEAK_FP64_FMA",
            "RMS_PEAK_GATHER", "RMS_PEAK_GATHER_DEP", "RMS_SERVE_STEPS", "RMS_SERVE_FILL"]
@@ -305,6 +305,14 @@ def rms_read_counts(run: Run) -> np.ndarray:
     return out
 
 
+def rms_read_slots(run: Run) -> np.ndarray:
+    """W int32: the walker (relative to walker_begin) in each slot of the
+    run's device state (identity unless RMS_MORTON)."""
+    out = np.zeros(run.n_walkers, np.int32)
+    run.status = check(L.lib.rms_read_slots(run.handle, out.ctypes.data), allow=(L.RMS_OK, L.RMS_W_LEAP_LIMIT))
+    return out
+
+
 def rms_run_step_time_ms(run: Run) -> float:
     ms = C.c_float()
     check(L.lib.rms_run_step_time_ms(run.handle, C.byref(ms)))
@@ -326,13 +334,14 @@ def rms_destroy_substrate(sub: Substrate) -> None:
 def simulate(wl, precision: int = RMS_FP64, n_walkers: Optional[int] = None, seed: Optional[int] = None,
              hash_: bool = False, walker_begin: int = 0, steps_per_launch: int = 0, walkers: bool = False,
              stream: Optional[int] = None, interaction: Optional[int] = None, checked: bool = False,
-             resume: Optional[dict] = None, step_end: int = 0, counts: bool = False) -> dict:
+             resume: Optional[dict] = None, step_end: int = 0, counts: bool = False, morton: bool = False) -> dict:
     """Run one workload (an rms_inputs.Workload) end to end through the C ABI.
     The interaction defaults to the workload's (elastic collision if unset);
     `leap_limit` in the result is True when an ERL step used up its draws.
     `resume` / `step_end` run part of the sequence (rms_run_range): a result
     with walkers=True and its `moments` is a state to resume from, given the
-    number of steps it took as `step`."""
+    number of steps it took as `step`.  `morton` re-buckets the walkers in
+    Morton order of their voxel before every step launch (RMS_MORTON)."""
     sub = rms_create_substrate(wl.labels, wl.voxel_um, wl.D, T2=wl.T2, T1=wl.T1, kappa=wl.kappa, dead=wl.dead,
                                periodic=wl.periodic, stream=stream, rho=getattr(wl, "rho", None),
                                conc=getattr(wl, "conc", None), lam=getattr(wl, "lam", -1.0),
@@ -342,7 +351,8 @@ def simulate(wl, precision: int = RMS_FP64, n_walkers: Optional[int] = None, see
     seq = rms_set_sequence(sub, wl.dt, G, wl.dirs, wl.b, wl.rec_steps, mode=wl.mode)
     run = rms_run(seq, wl.n_walkers if n_walkers is None else n_walkers, wl.seed if seed is None else seed,
                   precision,
-                  (RMS_TRAJ_HASH if hash_ else 0) | (RMS_CHECKED if checked else 0) | (RMS_COUNTS if counts else 0),
+                  (RMS_TRAJ_HASH if hash_ else 0) | (RMS_CHECKED if checked else 0) | (RMS_COUNTS if counts else 0)
+                  | (RMS_MORTON if morton else 0),
                   walker_begin,
                   steps_per_launch, stream,
                   int(getattr(wl, "interaction", RMS_EC)) if interaction is None else int(interaction),
@@ -355,6 +365,8 @@ def simulate(wl, precision: int = RMS_FP64, n_walkers: Optional[int] = None, see
         res.update(rms_read_walkers(run))
     if counts:
         res["counts"] = rms_read_counts(run)
+    if morton:
+        res["slots"] = rms_read_slots(run)
     run.close()
     seq.close()
     sub.close()

@@ -22,7 +22,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path
 UNITS = [("rms_api.cu", ["-fmad=false", "-Xcompiler", "-ffp-contract=off"]), ("walk_fp64.cu", ["-fmad=false"]), ("walk_fp32.cu", ["-fmad=true"]),
          ("walk_reject_fp64.cu", ["-fmad=false"]), ("walk_reject_fp32.cu", ["-fmad=true"]),
          ("walk_mt_fp64.cu", ["-fmad=false"]), ("walk_mt_fp32.cu", ["-fmad=true"]),
-         ("rms_noalloc.cu", ["-fmad=false"]), ("rms_serve.cu", ["-fmad=false"]), ("rms_peaks.cu", ["-fmad=false"])]
+         ("rms_noalloc.cu", ["-fmad=false"]), ("rms_morton.cu", []), ("rms_serve.cu", ["-fmad=false"]), ("rms_peaks.cu", ["-fmad=false"])]
 
 
 def _sources():

@@ -308,6 +308,7 @@ __global__ void init_kernel(Geometry g, const int32_t *ok_list, int64_t n_ok, co
     if (hash) st.hash[li] = 0ull;
     if (st.counts)
         for (int a = 0; a < 3; ++a) st.counts[(int64_t)a * ctl.n_walkers + li] = 0;
+    if (st.wid) st.wid[li] = (int32_t)li;
 }
 
 // ------------------------------------------------------------------ reductions
@@ -437,25 +438,27 @@ template <typename Real>
 __global__ void export_kernel(WalkerState<Real> st, int64_t W, int32_t S, bool hash, int32_t *i, double *o,
                               int32_t *i0, double *o0, int32_t *c, double *A, double *phase, uint64_t *h)
 {
-    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // slot
     if (w >= W) return;
+    const int64_t u = st.wid ? (int64_t)st.wid[w] : w;  // walker: the output row
+    if (u < 0 || u >= W) return;  // never, for a valid order (the read calls check the status first)
     for (int a = 0; a < 3; ++a) {
-        i[3 * w + a] = st.i0[a][w] + st.di[a][w];
-        o[3 * w + a] = (double)st.o[a][w];
-        i0[3 * w + a] = st.i0[a][w];
-        o0[3 * w + a] = (double)st.o0[a][w];
+        i[3 * u + a] = st.i0[a][w] + st.di[a][w];
+        o[3 * u + a] = (double)st.o[a][w];
+        i0[3 * u + a] = st.i0[a][w];
+        o0[3 * u + a] = (double)st.o0[a][w];
     }
-    c[w] = st.c[w];
+    c[u] = st.c[w];
     if (st.A_c)  // FP32 form: Kahan sum; kSaturatedF marks a saturated walker
-        A[w] = (float)st.A[w] >= kSaturatedF ? (double)INFINITY : (double)st.A[w] - (double)st.A_c[w];
+        A[u] = (float)st.A[w] >= kSaturatedF ? (double)INFINITY : (double)st.A[w] - (double)st.A_c[w];
     else
-        A[w] = (double)st.A[w];
+        A[u] = (double)st.A[w];
     for (int k = 0; k < S * 3; ++k) {
         double p = (double)st.phase[(int64_t)k * W + w];
         if (st.phase_c) p = p - (double)st.phase_c[(int64_t)k * W + w];
-        phase[(int64_t)w * S * 3 + k] = p;
+        phase[u * S * 3 + k] = p;
     }
-    h[w] = hash ? st.hash[w] : 0ull;
+    h[u] = hash ? st.hash[w] : 0ull;
 }
 
 // ------------------------------------------------------------------ substrate
@@ -858,7 +861,8 @@ extern "C" rms_status rms_destroy_sequence(rms_sequence *q)
 // ------------------------------------------------------------------ run
 
 template <typename Real>
-size_t rms::layout_state(WalkerState<Real> &st, char *base, int64_t W, int S, bool hash, bool f32, bool counts)
+size_t rms::layout_state(WalkerState<Real> &st, char *base, int64_t W, int S, bool hash, bool f32, bool counts,
+                         bool wid)
 {
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -877,6 +881,7 @@ size_t rms::layout_state(WalkerState<Real> &st, char *base, int64_t W, int S, bo
     st.phase_c = f32 ? (Real *)take(sizeof(Real) * W * S * 3) : nullptr;
     st.hash = hash ? (uint64_t *)take(sizeof(uint64_t) * W) : nullptr;
     st.counts = counts ? (int32_t *)take(sizeof(int32_t) * 3 * W) : nullptr;
+    st.wid = wid ? (int32_t *)take(sizeof(int32_t) * W) : nullptr;
     return off;
 }
 
@@ -990,7 +995,8 @@ rms_status rms::run_finalize(rms_run_handle *r)
 void rms::run_free(rms_run_handle *r, bool sync)
 {
     cudaStream_t s = r->stream;
-    void *p[] = {r->d_state, r->d_mom_partial, r->d_mom, r->d_ro_partial, r->d_S, r->d_status};
+    void *p[] = {r->d_state, r->d_state_alt, r->d_sort, r->d_mom_partial, r->d_mom, r->d_ro_partial, r->d_S,
+                 r->d_status};
     for (void *x : p)
         if (x) cudaFreeAsync(x, s);
     if (sync || r->h_cancel) cudaStreamSynchronize(s);
@@ -1008,8 +1014,10 @@ size_t rms::run_state_bytes(const rms_sequence *q, int64_t W, int32_t precision,
     const int64_t nc = (W + kRoChunk - 1) / kRoChunk;
     const int64_t ncombo = (int64_t)q->S * q->n_dirs * q->n_b;
     const bool cnt = (flags & RMS_COUNTS) != 0;
-    size_t b = precision == RMS_FP32 ? layout_state<float>(s32, nullptr, W, q->S, hash, true, cnt)
-                                     : layout_state<double>(s64, nullptr, W, q->S, hash, false, cnt);
+    const bool mort = (flags & RMS_MORTON) != 0;
+    size_t b = precision == RMS_FP32 ? layout_state<float>(s32, nullptr, W, q->S, hash, true, cnt, mort)
+                                     : layout_state<double>(s64, nullptr, W, q->S, hash, false, cnt, mort);
+    if (mort) b = 2 * b + morton_scratch_bytes(W);  // second state buffer and sort buffers
     b += sizeof(double) * ((size_t)std::max(q->n_rec, 1) * nb * kMoments + (size_t)std::max(q->n_rec, 1) * kMoments +
                            2 * (size_t)(ncombo + 1) * nc + 4 * (size_t)(ncombo + 1));
     return b;
@@ -1026,13 +1034,23 @@ rms_status rms::run_setup(rms_run_handle *r, bool with_cancel_and_events)
     r->n_combo = q->S * q->n_dirs * q->n_b;
     r->n_chunks = (int32_t)((r->W + kRoChunk - 1) / kRoChunk);
     const bool cnt = (r->flags & RMS_COUNTS) != 0;
-    const size_t bytes = f32 ? layout_state<float>(r->st32, nullptr, r->W, q->S, hash, true, cnt)
-                             : layout_state<double>(r->st64, nullptr, r->W, q->S, hash, false, cnt);
+    const bool mort = (r->flags & RMS_MORTON) != 0;
+    const size_t bytes = f32 ? layout_state<float>(r->st32, nullptr, r->W, q->S, hash, true, cnt, mort)
+                             : layout_state<double>(r->st64, nullptr, r->W, q->S, hash, false, cnt, mort);
     RMS_CUDA(cudaMallocAsync((void **)&r->d_state, bytes, s));
     if (f32)
-        layout_state<float>(r->st32, r->d_state, r->W, q->S, hash, true, cnt);
+        layout_state<float>(r->st32, r->d_state, r->W, q->S, hash, true, cnt, mort);
     else
-        layout_state<double>(r->st64, r->d_state, r->W, q->S, hash, false, cnt);
+        layout_state<double>(r->st64, r->d_state, r->W, q->S, hash, false, cnt, mort);
+    if (mort) {
+        RMS_CUDA(cudaMallocAsync((void **)&r->d_state_alt, bytes, s));
+        if (f32)
+            layout_state<float>(r->st32_alt, r->d_state_alt, r->W, q->S, hash, true, cnt, true);
+        else
+            layout_state<double>(r->st64_alt, r->d_state_alt, r->W, q->S, hash, false, cnt, true);
+        RMS_CUDA(cudaMallocAsync((void **)&r->d_sort, morton_scratch_bytes(r->W), s));
+        morton_plan(q->sub->nx, q->sub->ny, q->sub->nz, &r->sort_shift, &r->sort_passes);
+    }
     const size_t nmp = (size_t)std::max(q->n_rec, 1) * r->n_blocks * kMoments;
     RMS_CUDA(cudaMallocAsync((void **)&r->d_mom_partial, sizeof(double) * nmp, s));
     // zero: a run that ends before some recording steps reports zero sums for them
@@ -1100,6 +1118,7 @@ __global__ void import_kernel(WalkerState<Real> st, int64_t W, int32_t S, const 
     if (st.hash) st.hash[w] = hash ? hash[w] : 0ull;
     if (st.counts)
         for (int k = 0; k < 3; ++k) st.counts[(int64_t)k * W + w] = 0;
+    if (st.wid) st.wid[w] = (int32_t)w;
 }
 
 // Upload a stored state and seed the moment partials with the sums of the
@@ -1151,8 +1170,10 @@ static rms_status run_impl(rms_run_handle *r, int32_t spl, const rms_run_state *
     else
         RMS_TRY(run_init(r));
     RMS_CUDA(cudaEventRecord(r->ev_start, r->stream));
-    for (int64_t k0 = k_first; k0 < k_last; k0 += spl)
+    for (int64_t k0 = k_first; k0 < k_last; k0 += spl) {
+        if (r->flags & RMS_MORTON) RMS_TRY(run_rebucket(r));
         RMS_TRY(run_walk(r, k0, std::min<int64_t>(k_last, k0 + spl)));
+    }
     RMS_CUDA(cudaEventRecord(r->ev_end, r->stream));
     return run_finalize(r);
 }
@@ -1178,7 +1199,7 @@ extern "C" rms_status rms_run_range(rms_sequence *q, const rms_run_desc *d, cons
         return fail(RMS_E_INVALID_ARG, "n_walkers must be in [1, 2^31) and walker_begin >= 0");
     if (d->precision != RMS_FP64 && d->precision != RMS_FP32)
         return fail(RMS_E_INVALID_ARG, "precision must be RMS_FP64 or RMS_FP32");
-    if (d->flags & ~kVerifyFlags) return fail(RMS_E_INVALID_ARG, "unknown flag");
+    if (d->flags & ~(kVerifyFlags | RMS_MORTON)) return fail(RMS_E_INVALID_ARG, "unknown flag");
     if (d->steps_per_launch < 0) return fail(RMS_E_INVALID_ARG, "steps_per_launch must be >= 0");
     if (d->interaction != RMS_EC && d->interaction != RMS_RS && d->interaction != RMS_ERL)
         return fail(RMS_E_INVALID_ARG, "interaction must be RMS_EC, RMS_RS or RMS_ERL");
@@ -1232,6 +1253,9 @@ static rms_status finish(rms_run_handle *r)
     RMS_CUDA(cudaMemcpy(&status, r->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
     if (status & kErrInvariant)
         return fail(RMS_E_DEVICE, "a walker invariant broke (RMS_CHECKED); device status " + std::to_string(status));
+    if (status & kErrOrder)
+        return fail(RMS_E_DEVICE, "the walker re-ordering (RMS_MORTON) gave a slot out of range; device status " +
+                                      std::to_string(status));
     if (status & ~kWarnLeaps) return fail(RMS_E_DEVICE, "device status " + std::to_string(status));
     if (status & kWarnLeaps) {
         set_last_error("an ERL step found no admissible direction in RMS_MAX_LEAPS draws; "
@@ -1353,10 +1377,31 @@ extern "C" rms_status rms_read_counts(rms_run_handle *r, int64_t *counts)
     if (fin < 0) return fin;
     const int32_t *d = r->precision == RMS_FP32 ? r->st32.counts : r->st64.counts;
     if (!d) return fail(RMS_E_INVALID_ARG, "the run was made without RMS_COUNTS");
-    std::vector<int32_t> h((size_t)3 * r->W);
+    std::vector<int32_t> h((size_t)3 * r->W), wid;
     RMS_CUDA(cudaMemcpy(h.data(), d, sizeof(int32_t) * h.size(), cudaMemcpyDeviceToHost));
-    for (int64_t w = 0; w < r->W; ++w)
-        for (int a = 0; a < 3; ++a) counts[3 * w + a] = h[(size_t)a * r->W + w];
+    const int32_t *dw = r->precision == RMS_FP32 ? r->st32.wid : r->st64.wid;
+    if (dw) {  // RMS_MORTON: slot -> walker
+        wid.resize((size_t)r->W);
+        RMS_CUDA(cudaMemcpy(wid.data(), dw, sizeof(int32_t) * wid.size(), cudaMemcpyDeviceToHost));
+    }
+    for (int64_t w = 0; w < r->W; ++w) {
+        const int64_t u = dw ? wid[(size_t)w] : w;
+        for (int a = 0; a < 3; ++a) counts[3 * u + a] = h[(size_t)a * r->W + w];
+    }
+    return fin;
+}
+
+extern "C" rms_status rms_read_slots(rms_run_handle *r, int32_t *walker_of_slot)
+{
+    if (!r || !walker_of_slot) return fail(RMS_E_INVALID_ARG, "null argument");
+    const rms_status fin = finish(r);
+    if (fin < 0) return fin;
+    const int32_t *dw = r->precision == RMS_FP32 ? r->st32.wid : r->st64.wid;
+    if (dw) {
+        RMS_CUDA(cudaMemcpy(walker_of_slot, dw, sizeof(int32_t) * (size_t)r->W, cudaMemcpyDeviceToHost));
+    } else {
+        for (int64_t w = 0; w < r->W; ++w) walker_of_slot[w] = (int32_t)w;
+    }
     return fin;
 }
 

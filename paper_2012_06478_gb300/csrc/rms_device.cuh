@@ -84,7 +84,7 @@ constexpr int kMaxShapes = 8;
 
 // Device status bits: errors, and one warning (an ERL step that found no
 // admissible direction in kMaxLeaps draws; the walker stayed for that step).
-enum : int { kErrTimeout = 4, kWarnLeaps = 8, kErrInit = 16, kErrInvariant = 32 };
+enum : int { kErrTimeout = 4, kWarnLeaps = 8, kErrInit = 16, kErrInvariant = 32, kErrOrder = 64 };
 constexpr uint32_t kMaxInit = 4096;  // start draws per walker (spin concentrations)
 
 // A saturated walker (Sec. 2.1.3, magnetization transfer) has weight 0 for
@@ -111,6 +111,7 @@ struct WalkerState {
     Real *phase_c;     // Kahan compensation (FP32 form only), same layout
     uint64_t *hash;
     int32_t *counts;   // [3][W]: face events, crossings, reflections (RMS_COUNTS) or nullptr
+    int32_t *wid;      // walker (relative to the run's first) in each slot, or nullptr: the slot's index
 };
 
 struct Geometry {

@@ -74,6 +74,13 @@ struct rms_run_handle {
     char *d_state = nullptr;  // one allocation for the walker state
     rms::WalkerState<double> st64{};
     rms::WalkerState<float> st32{};
+    // RMS_MORTON: the second state buffer the re-bucketing gathers into, and
+    // the sort buffers (keys, slots, tile histograms, scan block sums)
+    char *d_state_alt = nullptr;
+    rms::WalkerState<double> st64_alt{};
+    rms::WalkerState<float> st32_alt{};
+    char *d_sort = nullptr;
+    int32_t sort_shift = 0, sort_passes = 0;
     double *d_mom_partial = nullptr, *d_mom = nullptr;
     // d_S: the unnormalised sums [combo][2] + (alpha sum, 0), then the
     // normalised signal in the same layout (normalised_S)
@@ -108,7 +115,8 @@ rms_status fail(rms_status st, const std::string &msg);
 inline double *normalised_S(const rms_run_handle *r) { return r->d_S + 2 * (size_t)(r->n_combo + 1); }
 
 template <typename Real>
-size_t layout_state(WalkerState<Real> &st, char *base, int64_t W, int S, bool hash, bool f32, bool counts);
+size_t layout_state(WalkerState<Real> &st, char *base, int64_t W, int S, bool hash, bool f32, bool counts,
+                    bool wid = false);
 
 // Run flags that select the verification kernel (checksum, invariant checks, counts).
 constexpr uint32_t kVerifyFlags = RMS_TRAJ_HASH | RMS_CHECKED | RMS_COUNTS;
@@ -120,6 +128,11 @@ rms_status run_walk(rms_run_handle *r, int64_t k0, int64_t k1);       // steps (
 rms_status run_finalize(rms_run_handle *r);                           // moments, read-out
 void run_free(rms_run_handle *r, bool sync);
 size_t run_state_bytes(const rms_sequence *q, int64_t W, int32_t precision, uint32_t flags);
+// RMS_MORTON (rms_morton.cu): the key's coordinate shift and radix passes for
+// a volume, the sort buffers' bytes, and the re-bucketing enqueued on r->stream.
+void morton_plan(int32_t nx, int32_t ny, int32_t nz, int32_t *shift, int32_t *passes);
+size_t morton_scratch_bytes(int64_t W);
+rms_status run_rebucket(rms_run_handle *r);
 template <typename Real>
 ReqDesc<Real> run_desc(rms_run_handle *r);
 

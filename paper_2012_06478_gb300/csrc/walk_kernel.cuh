@@ -298,7 +298,9 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
 
     const int64_t li = block * kWalkBlock + threadIdx.x;
     const bool active = li < ctl.n_walkers;
-    const uint64_t w = (uint64_t)(ctl.w_begin + li);
+    // the walker in this slot: its id picks its random streams (RMS_MORTON
+    // runs keep walkers in Morton order of their voxel, not in id order)
+    const uint64_t w = (uint64_t)(ctl.w_begin + ((active && st.wid) ? (int64_t)st.wid[li] : li));
     const int32_t N[3] = {g.nx, g.ny, g.nz};
     const int32_t stride[3] = {1, g.nx, g.nx * g.ny};
     const int32_t per[3] = {g.per_x, g.per_y, g.per_z};
@@ -757,15 +759,19 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
 // the compiler's choice).  The plain form's one-shape kernel: its integer-ALU
 // arithmetic is made of long dependent chains, whose latency more warps hide,
 // and 5 blocks (at most 102 registers) measured 6 % faster than the
-// unconstrained 4.  The FP32 form is left to the compiler (it settles on 7
-// blocks; a bound of 7, 8 or 9 measured no faster); kernels with more shapes
-// keep the registers their phases need.
-template <typename Real, int NS>
-constexpr int kWalkMinBlocks = (NS == 1 && std::is_same<Real, double>::value) ? 5 : 0;
+// unconstrained 4.  The FP32 form's one-shape elastic-collision kernel: 7
+// blocks (72 registers, no spills); left to the compiler it takes 80
+// registers since the walker id comes from the slot map (6 blocks, 4.8 %
+// slower).  The RS/ERL and absorbing-membrane kernels would spill under that
+// bound, and kernels with more shapes keep the registers their phases need.
+template <typename Real, int NS, int IM, bool MT>
+constexpr int kWalkMinBlocks = (NS != 1) ? 0
+                               : std::is_same<Real, double>::value ? 5
+                               : (IM == kInteractEC && !MT) ? 7 : 0;
 
 // One run: block b of the grid advances walkers b*kWalkBlock ... of the run.
 template <typename Real, int NS, bool HASH, int IM, bool MT>
-__global__ void __launch_bounds__(kWalkBlock, kWalkMinBlocks<Real, NS>)
+__global__ void __launch_bounds__(kWalkBlock, kWalkMinBlocks<Real, NS, IM, MT>)
 walk_kernel(Geometry g, Tables<Real> t, WalkerState<Real> st, RunCtl ctl, int64_t k_begin, int64_t k_end)
 {
     walk_block<Real, NS, HASH, IM, MT>(g, t, st, ctl, blockIdx.x, k_begin, k_end);
