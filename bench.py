@@ -374,7 +374,8 @@ def main():
         v = shard.allreduce_partials(shard.pack_partials(num32, res32[2], res32[1]))
         shard.unpack_partials(v, res32[0].shape, res32[1].shape)
 
-    spl = args.steps_per_launch or max(64, min(2_000_000_000 // W, wl.n_steps))
+    # the library's default launch size (about 8e9 walker-steps per launch with Morton re-bucketing)
+    spl = args.steps_per_launch or max(64, min((8_000_000_000 if args.morton else 2_000_000_000) // W, wl.n_steps))
     n_walk = math.ceil(wl.n_steps / spl)
     launches_per_step = 1 + n_walk + (1 if wl.rec_steps.size else 0) + 3
     if args.morton:  # per walk launch: the key, 5 kernels per radix pass, the permutation

@@ -58,7 +58,8 @@ typedef int rms_status;
 
 /* precision forms of rms_run */
 #define RMS_FP64 0 /* plain form: FP64 positions and phases, no FMA; bit-exact trajectories */
-#define RMS_FP32 1 /* precision form: voxel index + FP32 offset, FP32 Kahan phase, FP64 reductions */
+#define RMS_FP32 1 /* precision form: voxel index + FP32 offset, FP32 Kahan phase, FP64 reductions; the
+                      read-out's terms alpha e^{-i phi} in FP32 (within ~1e-5 of their FP64 sum, Eq. 7) */
 
 /* rms_run flags */
 #define RMS_TRAJ_HASH 1u /* keep a per-walker 64-bit checksum of the (step, voxel, label) sequence */
@@ -421,9 +422,9 @@ rms_status rms_philox4x32_10(const uint32_t *ctr, const uint32_t *key, int64_t n
 /* ------------------------------------------------------------------ */
 #define RMS_NOALLOC_SCRATCH_BYTES (8 * 1024 * 1024)
 
-/* The same read-out as rms_run's (S = sum alpha e^{-i phi} / sum alpha,
- * phi = q g.Phi_s, q = sqrt(b / b_s), alpha = exp(-A)) over walker data the
- * caller holds.  Every pointer is a DEVICE pointer of the current device:
+/* The same read-out as rms_run's in the plain FP64 form (S = sum alpha
+ * e^{-i phi} / sum alpha, phi = q g.Phi_s, q = sqrt(b / b_s), alpha =
+ * exp(-A), every term in FP64) over walker data the caller holds.  Every pointer is a DEVICE pointer of the current device:
  *   phase     : n_walkers*n_shapes*3 doubles, row-major (walker, shape, axis),
  *               the layout rms_read_walkers returns
  *   A         : n_walkers doubles, exponent of Eq. 5

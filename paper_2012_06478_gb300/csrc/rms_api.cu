@@ -313,7 +313,32 @@ __global__ void init_kernel(Geometry g, const int32_t *ok_list, int64_t n_ok, co
 
 // ------------------------------------------------------------------ reductions
 
-// Moments: fixed-order compensated sum of the per-block partials.
+// Moments, first level: the per-block partials of recording step r, blocks
+// c*kMomChunk ..., staged through shared memory with coalesced loads (the
+// partials of one recording step are contiguous), each of the 22 sums taken
+// in block order with compensation.  Block index = r * n_mchunks + c.
+constexpr int kMomChunk = 256;
+
+__global__ void __launch_bounds__(256) moments_chunk_kernel(const double *part, int32_t n_blocks, int32_t n_mchunks,
+                                                            double *out)
+{
+    __shared__ double tile[kMomChunk * kMoments];
+    const int64_t r = blockIdx.x / n_mchunks;
+    const int32_t c = blockIdx.x % n_mchunks;
+    const int32_t b0 = c * kMomChunk;
+    const int32_t nb = min(kMomChunk, n_blocks - b0);
+    const double *src = part + (r * n_blocks + b0) * kMoments;
+    for (int e = threadIdx.x; e < nb * kMoments; e += blockDim.x) tile[e] = src[e];
+    __syncthreads();
+    if (threadIdx.x < kMoments) {
+        double sum = 0.0, comp = 0.0;
+        for (int b = 0; b < nb; ++b) neumaier(sum, comp, tile[b * kMoments + threadIdx.x]);
+        out[(int64_t)blockIdx.x * kMoments + threadIdx.x] = sum + comp;
+    }
+}
+
+// Moments, second level: fixed-order compensated sum of the n_blocks
+// partials of each recording step (here the first level's chunk sums).
 __global__ void moments_reduce_kernel(const double *part, int32_t n_rec, int32_t n_blocks, double *out)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -382,6 +407,90 @@ readout_kernel(const Real *phase, const Real *phase_c, const Real *A, const Real
             }
         } else if (combo == n_combo) {
             for (int j = 0; j < nt; ++j) re += sAl[j];
+        }
+        __syncthreads();
+    }
+    if (combo <= n_combo) {
+        part[((int64_t)blockIdx.x * (n_combo + 1) + combo) * 2 + 0] = re;
+        part[((int64_t)blockIdx.x * (n_combo + 1) + combo) * 2 + 1] = im;
+    }
+}
+
+// A float widened to double, exactly, on the integer ALU for normal values
+// and zeros (the FP64 pipe is GB300's scarce one); subnormals, infinities and
+// NaNs take the hardware conversion, out of line so that it is not evaluated
+// speculatively beside the integer path.
+static __device__ __noinline__ double f2d_hw(float x) { return (double)x; }
+__device__ __forceinline__ double f2d(float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xFFu;
+    const uint64_t sign = (uint64_t)(b & 0x80000000u) << 32;
+    if (e == 0u) {
+        if ((b & 0x7FFFFFu) == 0u) return __longlong_as_double((long long)sign);  // +-0
+        return f2d_hw(x);
+    }
+    if (e == 0xFFu) return f2d_hw(x);
+    return __longlong_as_double((long long)(sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29)));
+}
+
+// The FP32 form's read-out: the same sums over the same chunks in the same
+// order, with each term alpha e^{-i phi} evaluated in single precision --
+// the phase staged as the float nearest to its compensated value, phi =
+// q (g . Phi_s) and sincosf in FP32, alpha rounded to float -- and summed in
+// FP64 (the term widened exactly).  With P = q sum_i |g_i| |Phi_i| every term
+// is within about (6 P + 4) 2^-24 alpha of its FP64 value, so S is within
+// (6 P + 4) 2^-24 of the FP64 read-out of the same walkers (7.4e-6 at
+// P = 20 rad), far inside the form's 1e-3 bar on S; the per-walker terms do
+// not depend on the walkers' order or chunking.  b = 0 (q = 0) takes alpha
+// in FP64, so S(b = 0) = 1 exactly, and the sum of alpha stays FP64.
+__global__ void __launch_bounds__(kRoBlock)
+readout_f32_kernel(const float *phase, const float *phase_c, const float *A, const float *A_c, int64_t W, int32_t S,
+                   const double *q, const double *dirs, int32_t n_dirs, int32_t n_b, int32_t n_combo, double *part)
+{
+    __shared__ float sP[kRoTile][kMaxShapes * 3];
+    __shared__ float sAl[kRoTile];
+    __shared__ double sAlD[kRoTile];
+    const int combo = blockIdx.y * kRoBlock + threadIdx.x;
+    int s = 0;
+    float qq = 0.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
+    if (combo < n_combo) {
+        const int ib = combo % n_b;
+        const int gi = (combo / n_b) % n_dirs;
+        s = combo / (n_b * n_dirs);
+        qq = (float)q[s * n_b + ib];
+        g0 = (float)dirs[3 * gi];
+        g1 = (float)dirs[3 * gi + 1];
+        g2 = (float)dirs[3 * gi + 2];
+    }
+    const int64_t w0 = (int64_t)blockIdx.x * kRoChunk;
+    const int64_t w1 = min(W, w0 + kRoChunk);
+    double re = 0.0, im = 0.0;
+    for (int64_t base = w0; base < w1; base += kRoTile) {
+        const int nt = (int)min((int64_t)kRoTile, w1 - base);
+        for (int e = threadIdx.x; e < nt * (S * 3 + 1); e += kRoBlock) {
+            const int j = e % nt, k = e / nt;
+            const int64_t w = base + j;
+            if (k < S * 3) {
+                sP[j][k] = (float)((double)phase[(int64_t)k * W + w] - (double)phase_c[(int64_t)k * W + w]);
+            } else {
+                // kSaturatedF (saturated): exp underflows to 0
+                const double al = exp(-((double)A[w] - (double)A_c[w]));
+                sAlD[j] = al;
+                sAl[j] = (float)al;
+            }
+        }
+        __syncthreads();
+        if (combo < n_combo && qq != 0.0f) {
+            for (int j = 0; j < nt; ++j) {
+                const float gp = fmaf(g2, sP[j][3 * s + 2], fmaf(g1, sP[j][3 * s + 1], g0 * sP[j][3 * s]));
+                float sn, cs;
+                sincosf(qq * gp, &sn, &cs);
+                re += f2d(sAl[j] * cs);
+                im += f2d(-(sAl[j] * sn));
+            }
+        } else if (combo <= n_combo) {  // b = 0, and the sum of alpha
+            for (int j = 0; j < nt; ++j) re += sAlD[j];
         }
         __syncthreads();
     }
@@ -964,6 +1073,8 @@ rms_status rms::run_walk(rms_run_handle *r, int64_t k0, int64_t k1)
     return r->precision == RMS_FP32 ? walk_impl<float>(r, k0, k1) : walk_impl<double>(r, k0, k1);
 }
 
+static int32_t mom_chunks(int32_t n_blocks) { return (n_blocks + kMomChunk - 1) / kMomChunk; }
+
 // Moment sums, the read-out and the normalisation, enqueued on the run's stream.
 template <typename Real>
 static rms_status finalize_impl(rms_run_handle *r)
@@ -972,13 +1083,20 @@ static rms_status finalize_impl(rms_run_handle *r)
     cudaStream_t s = r->stream;
     const WalkerState<Real> st = run_desc<Real>(r).st;
     if (q->n_rec > 0) {
-        moments_reduce_kernel<<<(q->n_rec * kMoments + 127) / 128, 128, 0, s>>>(r->d_mom_partial, q->n_rec,
-                                                                                r->n_blocks, r->d_mom);
+        const int32_t nmc = mom_chunks(r->n_blocks);
+        moments_chunk_kernel<<<(unsigned)((int64_t)q->n_rec * nmc), 256, 0, s>>>(r->d_mom_partial, r->n_blocks, nmc,
+                                                                              r->d_mom_chunk);
+        moments_reduce_kernel<<<(q->n_rec * kMoments + 127) / 128, 128, 0, s>>>(r->d_mom_chunk, q->n_rec, nmc,
+                                                                                r->d_mom);
         RMS_CUDA(cudaGetLastError());
     }
     const dim3 rgrid((unsigned)r->n_chunks, (unsigned)((r->n_combo + 1 + kRoBlock - 1) / kRoBlock));
-    readout_kernel<Real><<<rgrid, kRoBlock, 0, s>>>(st.phase, st.phase_c, st.A, st.A_c, r->W, q->S, q->d_q,
-                                                    q->d_dirs, q->n_dirs, q->n_b, r->n_combo, r->d_ro_partial);
+    if constexpr (std::is_same<Real, float>::value)
+        readout_f32_kernel<<<rgrid, kRoBlock, 0, s>>>(st.phase, st.phase_c, st.A, st.A_c, r->W, q->S, q->d_q,
+                                                      q->d_dirs, q->n_dirs, q->n_b, r->n_combo, r->d_ro_partial);
+    else
+        readout_kernel<Real><<<rgrid, kRoBlock, 0, s>>>(st.phase, st.phase_c, st.A, st.A_c, r->W, q->S, q->d_q,
+                                                        q->d_dirs, q->n_dirs, q->n_b, r->n_combo, r->d_ro_partial);
     readout_reduce_kernel<<<(r->n_combo + 1 + 127) / 128, 128, 0, s>>>(r->d_ro_partial, r->n_chunks, r->n_combo,
                                                                        r->d_S);
     normalise_kernel<<<(r->n_combo + 1 + 127) / 128, 128, 0, s>>>(r->d_S, r->n_combo, normalised_S(r));
@@ -995,8 +1113,8 @@ rms_status rms::run_finalize(rms_run_handle *r)
 void rms::run_free(rms_run_handle *r, bool sync)
 {
     cudaStream_t s = r->stream;
-    void *p[] = {r->d_state, r->d_state_alt, r->d_sort, r->d_mom_partial, r->d_mom, r->d_ro_partial, r->d_S,
-                 r->d_status};
+    void *p[] = {r->d_state, r->d_state_alt, r->d_sort, r->d_mom_partial, r->d_mom_chunk, r->d_mom, r->d_ro_partial,
+                 r->d_S, r->d_status};
     for (void *x : p)
         if (x) cudaFreeAsync(x, s);
     if (sync || r->h_cancel) cudaStreamSynchronize(s);
@@ -1019,6 +1137,7 @@ size_t rms::run_state_bytes(const rms_sequence *q, int64_t W, int32_t precision,
                                      : layout_state<double>(s64, nullptr, W, q->S, hash, false, cnt, mort);
     if (mort) b = 2 * b + morton_scratch_bytes(W);  // second state buffer and sort buffers
     b += sizeof(double) * ((size_t)std::max(q->n_rec, 1) * nb * kMoments + (size_t)std::max(q->n_rec, 1) * kMoments +
+                           (size_t)std::max(q->n_rec, 1) * mom_chunks((int32_t)nb) * kMoments +
                            2 * (size_t)(ncombo + 1) * nc + 4 * (size_t)(ncombo + 1));
     return b;
 }
@@ -1056,6 +1175,8 @@ rms_status rms::run_setup(rms_run_handle *r, bool with_cancel_and_events)
     // zero: a run that ends before some recording steps reports zero sums for them
     RMS_CUDA(cudaMemsetAsync(r->d_mom_partial, 0, sizeof(double) * nmp, s));
     RMS_CUDA(cudaMallocAsync((void **)&r->d_mom, sizeof(double) * std::max(q->n_rec, 1) * kMoments, s));
+    RMS_CUDA(cudaMallocAsync((void **)&r->d_mom_chunk,
+                             sizeof(double) * std::max(q->n_rec, 1) * mom_chunks(r->n_blocks) * kMoments, s));
     RMS_CUDA(cudaMallocAsync((void **)&r->d_ro_partial, sizeof(double) * 2 * (size_t)(r->n_combo + 1) * r->n_chunks, s));
     RMS_CUDA(cudaMallocAsync((void **)&r->d_S, sizeof(double) * 4 * (r->n_combo + 1), s));
     RMS_CUDA(cudaMallocAsync((void **)&r->d_status, sizeof(int32_t), s));
@@ -1215,7 +1336,9 @@ extern "C" rms_status rms_run_range(rms_sequence *q, const rms_run_desc *d, cons
     r->stream = (cudaStream_t)d->stream;
     int32_t spl = d->steps_per_launch;
     if (spl == 0) {
-        const int64_t target = 2000000000ll / std::max<int64_t>(r->W, 1);
+        // about 2e9 walker-steps per launch (a few tens of ms); 8e9 with Morton
+        // re-bucketing, which runs once per launch (locality holds that long)
+        const int64_t target = ((r->flags & RMS_MORTON) ? 8000000000ll : 2000000000ll) / std::max<int64_t>(r->W, 1);
         spl = (int32_t)std::max<int64_t>(64, std::min<int64_t>(target, std::max<int64_t>(q->n_steps, 1)));
     }
     rms_status st = run_impl(r, spl, from, k_first, k_last);

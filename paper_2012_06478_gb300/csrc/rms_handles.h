@@ -82,6 +82,7 @@ struct rms_run_handle {
     char *d_sort = nullptr;
     int32_t sort_shift = 0, sort_passes = 0;
     double *d_mom_partial = nullptr, *d_mom = nullptr;
+    double *d_mom_chunk = nullptr;  // first-level moment sums [rec][chunk of 256 blocks][22]
     // d_S: the unnormalised sums [combo][2] + (alpha sum, 0), then the
     // normalised signal in the same layout (normalised_S)
     double *d_ro_partial = nullptr, *d_S = nullptr;

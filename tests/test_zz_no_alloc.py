@@ -7,7 +7,10 @@ streams, where cudaMalloc/cudaFree could synchronise the device; an
 application whose device memory all sits in its own fixed pool).  The caller
 owns every input and output buffer -- here torch tensors -- and the library
 uses only its fixed internal scratch.  Two calls in a row, on different
-runs, must each match the regular path.  This file is collected last.
+runs, must each match the regular path: to 1e-12 for a plain FP64 run, whose
+read-out has the same FP64 terms, and, for an FP32-form run (whose read-out
+evaluates each term in single precision), within the bound of that read-out
+that tests/test_gpu_readout.py uses.  This file is collected last.
 """
 import ctypes as C
 
@@ -15,6 +18,7 @@ import numpy as np
 import pytest
 
 from conftest import make_workload
+from test_gpu_readout import FP32_READOUT_TOL
 
 pytestmark = pytest.mark.gpu
 
@@ -65,8 +69,11 @@ def test_noalloc_readout_matches_regular_readout_twice():
         bs = rms.rms_sequence_bvalues(seq)
         rc, S, asum = _noalloc(torch, _lib.lib, st, bs, wl)
         assert rc == _lib.RMS_OK, _lib.last_error()
-        err = np.abs(S - S_ref) / np.maximum(np.abs(S_ref), 1e-3)
-        assert err.max() <= 1e-12, err.max()
+        if prec == rms.RMS_FP64:
+            err = np.abs(S - S_ref) / np.maximum(np.abs(S_ref), 1e-3)
+            assert err.max() <= 1e-12, err.max()
+        else:
+            assert np.abs(S - S_ref).max() <= FP32_READOUT_TOL, np.abs(S - S_ref).max()
         assert abs(asum - asum_ref) <= 1e-12 * asum_ref
         run.close()
         seq.close()
