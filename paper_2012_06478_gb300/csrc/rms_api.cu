@@ -1022,6 +1022,7 @@ ReqDesc<Real> rms::run_desc(rms_run_handle *r)
     d.ctl.cancel = r->d_cancel;
     d.ctl.mom_partial = r->d_mom_partial;
     d.ctl.n_blocks = r->n_blocks;
+    round_keys(r->seed, d.ctl.rk);
     return d;
 }
 template ReqDesc<float> rms::run_desc<float>(rms_run_handle *);

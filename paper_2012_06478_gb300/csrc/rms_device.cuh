@@ -30,6 +30,35 @@ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1)
     return c;
 }
 
+// The same generator with the ten rounds' keys given: rk[2r], rk[2r + 1] =
+// the key after r Weyl increments (round_keys below).  The step kernel reads
+// them from its launch parameters, where they cost no instruction per draw.
+constexpr int kRoundKeys = 20;
+
+__device__ __forceinline__ U4 philox4x32_10_rk(U4 c, const uint32_t *rk)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = U4{hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0};
+    }
+    return c;
+}
+
+__host__ __device__ inline void round_keys(uint64_t seed, uint32_t *rk)
+{
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = k0;
+        rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
 // Counter layout: key (seed_lo, seed_hi); counter (walker_lo, walker_hi,
 // step, tag << 16 | call).
 enum : uint32_t { kTagInit = 1u, kTagDir = 2u, kTagPerm = 3u, kTagMT = 4u };
@@ -149,6 +178,7 @@ struct RunCtl {
     const volatile int32_t *cancel; // host-mapped cancel flag (nullptr = none)
     double *mom_partial;            // [rec][block][22]
     int32_t n_blocks;
+    uint32_t rk[kRoundKeys];        // Philox round keys of seed (round_keys)
 };
 
 // One request of a batched launch: everything the walk needs.
