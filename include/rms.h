@@ -329,7 +329,8 @@ rms_status rms_read_slots(rms_run_handle *run, int32_t *walker_of_slot);
 rms_status rms_destroy_run(rms_run_handle *run);
 
 /* Device time (ms) between the start of the first and the end of the last
- * step launch of a finished run; synchronises. */
+ * step launch of a finished run (with RMS_MORTON, the re-orderings before
+ * each launch included); synchronises. */
 rms_status rms_run_step_time_ms(rms_run_handle *run, float *ms);
 
 /* ------------------------------------------------------------------ */
