@@ -248,20 +248,39 @@ __device__ __forceinline__ void neumaier(double &sum, double &comp, double x)
 }
 
 // b of a unit waveform: b_s = dt sum_{j=1..N} F_{j-1}^2, F_j = F_{j-1} + dt G_j
-// (compensated sum); then q = sqrt(b / b_s), the amplitude giving b.
-__global__ void bvalue_kernel(int64_t N, int32_t S, double dt, const double *G, int32_t n_b, const double *b,
-                              double *bs_out, double *q)
+// (compensated sum); then q = sqrt(b / b_s), the amplitude giving b.  One
+// block per shape: the block stages the waveform through shared memory in
+// coalesced chunks and thread 0 takes the recurrence in step order -- the
+// CPU reference's operations in its order, so b_s is the same to the bit.
+// (Read straight from global memory, each step waited for its load: 34 ms
+// for N = 1e5, most of a sequence's set-up.)
+constexpr int kBvThreads = 256;
+constexpr int kBvChunk = 2048;
+
+__global__ void __launch_bounds__(kBvThreads) bvalue_kernel(int64_t N, int32_t S, double dt, const double *G,
+                                                            int32_t n_b, const double *b, double *bs_out, double *q)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    double F = 0.0, sum = 0.0, comp = 0.0;
-    for (int64_t j = 1; j <= N; ++j) {
-        neumaier(sum, comp, F * F);
-        F = F + dt * G[(int64_t)s * N + (j - 1)];
+    const int s = blockIdx.x;
+    if (s >= S) return;  // block-uniform
+    __shared__ double sg[kBvChunk];
+    const double *g = G + (int64_t)s * N;
+    double F = 0.0, sum = 0.0, comp = 0.0;  // thread 0's
+    for (int64_t base = 0; base < N; base += kBvChunk) {
+        const int n = (int)min((int64_t)kBvChunk, N - base);
+        for (int i = threadIdx.x; i < n; i += kBvThreads) sg[i] = g[base + i];
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int i = 0; i < n; ++i) {
+                neumaier(sum, comp, F * F);
+                F = F + dt * sg[i];
+            }
+        __syncthreads();
     }
-    const double bs = dt * (sum + comp);
-    bs_out[s] = bs;
-    for (int i = 0; i < n_b; ++i) q[s * n_b + i] = bs > 0.0 ? sqrt(b[i] / bs) : 0.0;
+    if (threadIdx.x == 0) {
+        const double bs = dt * (sum + comp);
+        bs_out[s] = bs;
+        for (int i = 0; i < n_b; ++i) q[s * n_b + i] = bs > 0.0 ? sqrt(b[i] / bs) : 0.0;
+    }
 }
 
 // ------------------------------------------------------------------ init (Sec. 2.2 item 1)
@@ -905,7 +924,8 @@ static rms_status set_sequence_impl(rms_substrate *sub, const rms_sequence_desc 
         step_tables_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, S, d->dt_ms, d_G, d_rec, d->n_rec,
                                                                          q->d_wG64, q->d_wG32, q->d_flags,
                                                                          q->d_rec_of);
-    bvalue_kernel<<<1, 32, 0, st>>>(N, S, d->dt_ms, d_G, d->n_b, q->d_b, q->d_bs, q->d_q);
+    bvalue_kernel<<<(unsigned)std::max(S, 1), kBvThreads, 0, st>>>(N, S, d->dt_ms, d_G, d->n_b, q->d_b, q->d_bs,
+                                                                    q->d_q);
     RMS_CUDA(cudaGetLastError());
     int32_t w = 0;
     RMS_CUDA(cudaMemcpyAsync(&w, d_warn, sizeof(int32_t), cudaMemcpyDeviceToHost, st));

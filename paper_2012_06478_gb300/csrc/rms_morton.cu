@@ -235,15 +235,38 @@ void morton_plan(int32_t nx, int32_t ny, int32_t nz, int32_t *shift, int32_t *pa
     *passes = (3 * (bits - s) + 7) / 8;
 }
 
-size_t morton_scratch_bytes(int64_t W)
+// The sort buffers of W walkers, carved from one allocation (base nullptr:
+// sizes only): keys and slots twice (ping-pong between passes), the tile
+// histograms [256][n_tiles] and the scan's block sums, each 256-byte aligned.
+struct SortBuffers {
+    uint32_t *key[2];
+    int32_t *val[2];
+    uint32_t *hist, *bsum;
+    int64_t n_tiles, M, nb;
+    size_t bytes;
+};
+
+static SortBuffers sort_buffers(char *base, int64_t W)
 {
-    const int64_t n_tiles = (W + kSortTile - 1) / kSortTile;
-    const int64_t M = 256 * n_tiles;
-    const int64_t nb = (M + kScanSpan - 1) / kScanSpan;
-    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
-    return 2 * up(sizeof(uint32_t) * W) + 2 * up(sizeof(int32_t) * W) + up(sizeof(uint32_t) * M) +
-           up(sizeof(uint32_t) * nb);
+    SortBuffers b{};
+    b.n_tiles = (W + kSortTile - 1) / kSortTile;
+    b.M = 256 * b.n_tiles;
+    b.nb = (b.M + kScanSpan - 1) / kScanSpan;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *q = base ? base + off : nullptr;
+        off += (bytes + 255) & ~size_t(255);
+        return q;
+    };
+    for (int i = 0; i < 2; ++i) b.key[i] = (uint32_t *)take(sizeof(uint32_t) * W);
+    for (int i = 0; i < 2; ++i) b.val[i] = (int32_t *)take(sizeof(int32_t) * W);
+    b.hist = (uint32_t *)take(sizeof(uint32_t) * b.M);
+    b.bsum = (uint32_t *)take(sizeof(uint32_t) * b.nb);
+    b.bytes = off;
+    return b;
 }
+
+size_t morton_scratch_bytes(int64_t W) { return sort_buffers(nullptr, W).bytes; }
 
 template <typename Real>
 static rms_status rebucket_impl(rms_run_handle *r, WalkerState<Real> &st, WalkerState<Real> &alt)
@@ -251,24 +274,11 @@ static rms_status rebucket_impl(rms_run_handle *r, WalkerState<Real> &st, Walker
     if (r->sort_passes <= 0) return RMS_OK;  // one voxel: nothing to order
     cudaStream_t s = r->stream;
     const int64_t W = r->W;
-    const int64_t n_tiles = (W + kSortTile - 1) / kSortTile;
-    const int64_t M = 256 * n_tiles;
-    const int64_t nb = (M + kScanSpan - 1) / kScanSpan;
-    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
-    char *p = r->d_sort;
-    uint32_t *key[2];
-    int32_t *val[2];
-    key[0] = (uint32_t *)p;
-    p += up(sizeof(uint32_t) * W);
-    key[1] = (uint32_t *)p;
-    p += up(sizeof(uint32_t) * W);
-    val[0] = (int32_t *)p;
-    p += up(sizeof(int32_t) * W);
-    val[1] = (int32_t *)p;
-    p += up(sizeof(int32_t) * W);
-    uint32_t *hist = (uint32_t *)p;
-    p += up(sizeof(uint32_t) * M);
-    uint32_t *bsum = (uint32_t *)p;
+    const SortBuffers b = sort_buffers(r->d_sort, W);
+    uint32_t *const *key = b.key;
+    int32_t *const *val = b.val;
+    uint32_t *hist = b.hist, *bsum = b.bsum;
+    const int64_t n_tiles = b.n_tiles, M = b.M, nb = b.nb;
 
     const rms_substrate *sub = r->seq->sub;
     const unsigned g256 = (unsigned)((W + 255) / 256);

@@ -147,3 +147,20 @@ def test_normalise_partials_on_the_host():
     assert _lib.lib.rms_normalise_partials(-1, None, None, 1.0, None, None) == _lib.RMS_E_INVALID_ARG
     assert _lib.lib.rms_normalise_partials(3, None, None, 1.0, None, None) == _lib.RMS_E_INVALID_ARG
     assert _lib.lib.rms_normalise_partials(0, None, None, 1.0, None, None) == _lib.RMS_OK
+
+
+def test_binding_constants_match_the_header():
+    """Every integer #define of include/*.h that the ctypes binding also
+    defines has the same value there (status codes, precision forms, run
+    flags, interactions, serving policies, peak kinds)."""
+    from paper_2012_06478_gb300 import _lib
+    seen = 0
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        for name, val in re.findall(r"^#define\s+(RMS_[A-Z0-9_]+)\s+\(?(-?\d+)u?\)?\s", open(
+                os.path.join(ROOT, "include", fn)).read(), re.M):
+            if hasattr(_lib, name):
+                assert getattr(_lib, name) == int(val), (name, getattr(_lib, name), val)
+                seen += 1
+    assert seen >= 25, seen
