@@ -377,7 +377,8 @@ def main():
     # the library's default launch size (about 8e9 walker-steps per launch with Morton re-bucketing)
     spl = args.steps_per_launch or max(64, min((8_000_000_000 if args.morton else 2_000_000_000) // W, wl.n_steps))
     n_walk = math.ceil(wl.n_steps / spl)
-    launches_per_step = 1 + n_walk + (1 if wl.rec_steps.size else 0) + 3
+    # init, the walk launches, the two levels of the moment reduction, read-out, its reduction, normalisation
+    launches_per_step = 1 + n_walk + (2 if wl.rec_steps.size else 0) + 3
     if args.morton:  # per walk launch: the key, 5 kernels per radix pass, the permutation
         launches_per_step += n_walk * (2 + 5 * morton_passes(wl.shape_xyz))
     sm_mhz = clk.summary().get("sm_mhz") or pk.get("sm_max_mhz") or 2070.0
