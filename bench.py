@@ -471,7 +471,7 @@ def method_ops(wl):
     multiply, a three-input logical op, a fused multiply-add and a load each
     count one).
       Philox4x32-10 (one call per step): 10 rounds x (2 wide multiplies,
-        2 three-input XORs, 2 key additions)                          60
+        2 three-input XORs); the round keys are constants of the run   40
       direction: z, r = sqrt((1-z)(1+z)), octant reduction, azimuth
         polynomials of degree 7/8, octant map, scaling                 28
       step vector d = n s_c                                            3
@@ -484,7 +484,7 @@ def method_ops(wl):
       relaxation (a finite T1 or T2 somewhere): Kahan add               4
       step loop and flag load                                          3"""
     ev, g_frac, S, relax = _step_profile(wl)
-    return 60 + 28 + 3 + 12 + 13 * ev + 6 + g_frac * (12 + 15 * S) + (4 if relax else 0) + 3
+    return 40 + 28 + 3 + 12 + 13 * ev + 6 + g_frac * (12 + 15 * S) + (4 if relax else 0) + 3
 
 
 def fp64_ops(wl):

@@ -89,7 +89,7 @@ def test_operation_counts_of_the_axon_workload():
     ev, g_frac, S, relax = bench._step_profile(wl)
     assert abs(ev - 1.5 * math.sqrt(6 * 2.0 * 2e-4) / 0.1) < 1e-12   # one D everywhere
     assert abs(g_frac - 0.5) < 1e-12 and S == 1 and not relax
-    assert abs(bench.method_ops(wl) - (60 + 28 + 3 + 12 + 13 * ev + 6 + 0.5 * (12 + 15) + 3)) < 1e-9
+    assert abs(bench.method_ops(wl) - (40 + 28 + 3 + 12 + 13 * ev + 6 + 0.5 * (12 + 15) + 3)) < 1e-9
     assert abs(bench.fp64_ops(wl) - (20 + 3 + 4.5 + 5 * ev + 7 + 0.5 * (12 + 6))) < 1e-9
 
 
