@@ -775,19 +775,21 @@ __device__ __forceinline__ void walk_block(const Geometry &g, const Tables<Real>
 // the compiler's choice).  The plain form's one-shape kernel: its integer-ALU
 // arithmetic is made of long dependent chains, whose latency more warps hide,
 // and 5 blocks (at most 102 registers) measured 6 % faster than the
-// unconstrained 4.  The FP32 form's one-shape elastic-collision kernel: 7
-// blocks (72 registers, no spills); left to the compiler it takes 80
-// registers since the walker id comes from the slot map (6 blocks, 4.8 %
-// slower).  The RS/ERL and absorbing-membrane kernels would spill under that
-// bound, and kernels with more shapes keep the registers their phases need.
-template <typename Real, int NS, int IM, bool MT>
+// unconstrained 4.  The FP32 form's one-shape elastic-collision kernel: 9
+// blocks (56 registers, no spills; 36 warps per SM), 2.5 % faster than 7
+// blocks (72 registers) and 7.5 % faster than the compiler's own choice (80
+// registers, 6 blocks); 10 blocks spill.  The RS/ERL and absorbing-membrane
+// kernels would spill under such bounds, and kernels with more shapes keep
+// the registers their phases need.
+template <typename Real, int NS, bool HASH, int IM, bool MT>
 constexpr int kWalkMinBlocks = (NS != 1) ? 0
                                : std::is_same<Real, double>::value ? 5
-                               : (IM == kInteractEC && !MT) ? 7 : 0;
+                               : (IM != kInteractEC || MT) ? 0
+                               : HASH ? 7 : 9;  // the verification kernel would spill at 9
 
 // One run: block b of the grid advances walkers b*kWalkBlock ... of the run.
 template <typename Real, int NS, bool HASH, int IM, bool MT>
-__global__ void __launch_bounds__(kWalkBlock, kWalkMinBlocks<Real, NS, IM, MT>)
+__global__ void __launch_bounds__(kWalkBlock, kWalkMinBlocks<Real, NS, HASH, IM, MT>)
 walk_kernel(Geometry g, Tables<Real> t, WalkerState<Real> st, RunCtl ctl, int64_t k_begin, int64_t k_end)
 {
     walk_block<Real, NS, HASH, IM, MT, true>(g, t, st, ctl, blockIdx.x, k_begin, k_end);
