@@ -70,7 +70,7 @@ def test_events_per_step_matches_the_oracle_counts(oracle_lib):
 
 def test_every_library_name_bench_uses_exists():
     """bench.py reaches the library only through the package: every `rms.X`
-    it names is exported (caught on the CPU, not on the GPU machine)."""
+    it names is exported (caught on the CPU, before any GPU run)."""
     import re
     import paper_2012_06478_gb300 as rms
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
