@@ -142,3 +142,17 @@ def test_fp32_vs_fp64_verdicts_at_every_recording_time():
     assert bad["dK_worst"]["axis"] == "y" and abs(bad["dK_worst"]["t_ms"] - t[3]) < 1e-12
     assert abs(bad["dK_worst"]["K64"] - 0.5) < 1e-9
     assert bad["per_time"]["dK_over_bar"][3] > 1 and max(bad["per_time"]["dK_over_bar"][:3]) == 0
+
+
+def test_morton_passes_and_launch_count():
+    """The radix passes bench.py counts for RMS_MORTON: 3 key bits per bit of
+    the largest coordinate, coordinates shifted to at most 8 bits, 8 key bits
+    per pass (a 32^3 volume: 15 key bits, 2 passes; 200x200x400 and 512^3:
+    24 key bits, 3 passes; one voxel: no pass)."""
+    bench = _bench()
+    assert bench.morton_passes((32, 32, 32)) == 2
+    assert bench.morton_passes((200, 200, 400)) == 3
+    assert bench.morton_passes((512, 512, 512)) == 3
+    assert bench.morton_passes((1024, 1024, 1024)) == 3
+    assert bench.morton_passes((4, 4, 4)) == 1
+    assert bench.morton_passes((1, 1, 1)) == 0
