@@ -79,8 +79,10 @@ typedef int rms_status;
                             Changes no trajectory (the random streams follow the walker id, not its
                             place in memory) and nothing rms_read_walkers / rms_read_counts return;
                             only the order of the sums over walkers (signal and moment sums agree to
-                            rounding).  Costs a second copy of the walker state and 16 bytes per
-                            walker of sort buffers, and about 1-2 % of a launch of 2e9 walker-steps. */
+                            rounding).  Costs a second copy of the walker state and about 17 bytes
+                            per walker of sort buffers.  With this flag the default launch covers
+                            about 8e9 walker-steps (steps_per_launch 0), and one re-ordering of 1e7
+                            walkers takes about 1.3 % of it. */
 
 /* Particle-membrane interaction of rms_run (Sec. 2.1.2).  A face is "refused"
  * when it is impermeable (a label pair with kappa = 0, a dead label, the wall
