@@ -76,7 +76,7 @@ typedef int rms_status;
                             first shifted right to 8 bits), so that walkers next to each other in
                             memory look up neighbouring parts of the label volume (Sec. 2.1.1: the
                             volume is the lookup table).  For volumes about the size of the L2
-                            cache or larger (measured: +23 % at 128 MB, +14 % at 256 MiB, no
+                            cache or larger (measured: +23 % at 128 MB, +10 % at 256 MiB, no
                             change at 32 MB).
                             Changes no trajectory (the random streams follow the walker id, not its
                             place in memory) and nothing rms_read_walkers / rms_read_counts return;
